@@ -1,0 +1,623 @@
+/*
+ * CPU oracle for maximal biclique enumeration.
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library's product path may call
+ * this code: it exists so that tests, the smoke check and the benchmark's
+ * CPU-baseline leg can judge the GPU path. It shares no source with the GPU
+ * path.
+ *
+ * What it computes (paper Section II-A, problem definition): for a bipartite
+ * graph G = (U u V, E), every pair (R, L) with R a nonempty subset of U and
+ * L a nonempty subset of V such that every u in R is adjacent to every v in
+ * L, and no vertex outside the pair can be added on either side. With
+ * Gamma(X) the common neighbours of X, these are exactly the pairs with
+ * L = Gamma(R) and R = Gamma(L).
+ *
+ * How (paper Section II-B, Algorithm 1, MBEA): plain recursive backtracking
+ * over the four sets L (subset of V), R, P, Q (subsets of U), written with
+ * sorted int32 arrays and binary-search intersections, no bitsets, no
+ * blocking, no pruning beyond the algorithm's own steps.
+ *
+ * Readings of points the paper leaves open:
+ *  - Initial call: L = V, R = {}, P = U without isolated vertices, Q = {}.
+ *    An isolated candidate would give L' = {} and a degenerate pair.
+ *  - Candidate selection pops from P the vertex with the smallest
+ *    |N(v) n L| (ascending order, Section II-C "candidate selection"),
+ *    ties broken by the smaller vertex id. L is fixed for the whole while
+ *    loop of one call, so these keys do not change while the loop runs and
+ *    the sequence of pops is P sorted by (|N(v) n L|, id); the oracle sorts
+ *    once per call instead of rescanning P before every pop.
+ *  - A vertex of P that joins R' stays in P (no L - L' removal, no pivots).
+ *  - "nodes" counts the iterations of the while loop (every candidate that
+ *    was popped, including those whose node fails the maximality check).
+ *
+ * Output digest: count = number of maximal bicliques; hash = sum over them,
+ * modulo 2^64, of SM( sum_{u in R} SM(2u) + sum_{v in L} SM(2v+1) ), where
+ * SM is one SplitMix64 output step (Steele, Lea & Flood, OOPSLA 2014):
+ * add the golden gamma 0x9e3779b97f4a7c15, then the variant-13 mix.
+ */
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ hash */
+
+uint64_t orc_sm(uint64_t z)
+{
+    z += 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static uint64_t key_u(int32_t u) { return orc_sm(2ULL * (uint64_t)u); }
+static uint64_t key_v(int32_t v) { return orc_sm(2ULL * (uint64_t)v + 1ULL); }
+
+/* ---------------------------------------------------------------- arrays */
+
+typedef struct {
+    int32_t *a;
+    int64_t n, cap;
+} ovec;
+
+static int ov_push(ovec *v, int32_t x)
+{
+    if (v->n == v->cap) {
+        int64_t nc = v->cap ? v->cap * 2 : 16;
+        int32_t *na = (int32_t *)realloc(v->a, (size_t)nc * sizeof(int32_t));
+        if (!na) return -1;
+        v->a = na;
+        v->cap = nc;
+    }
+    v->a[v->n++] = x;
+    return 0;
+}
+
+static void ov_free(ovec *v)
+{
+    free(v->a);
+    v->a = NULL;
+    v->n = v->cap = 0;
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* ----------------------------------------------------------------- graph */
+
+typedef struct {
+    int32_t nU, nV;
+    const int32_t *u_off, *u_adj; /* N(u) for u in U, sorted V ids */
+    const int32_t *v_off, *v_adj; /* N(v) for v in V, sorted U ids */
+} ograph;
+
+static const int32_t *nbr(const ograph *g, int32_t u, int64_t *deg)
+{
+    *deg = g->u_off[u + 1] - g->u_off[u];
+    return g->u_adj + g->u_off[u];
+}
+
+static int contains(const int32_t *a, int64_t n, int32_t x)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < n && a[lo] == x;
+}
+
+/* |A n B| for sorted A, B: look every element of the shorter up in the longer */
+static int64_t count_common(const int32_t *a, int64_t na, const int32_t *b, int64_t nb)
+{
+    if (na > nb) {
+        const int32_t *t = a;
+        a = b;
+        b = t;
+        int64_t tn = na;
+        na = nb;
+        nb = tn;
+    }
+    int64_t c = 0;
+    for (int64_t i = 0; i < na; ++i) c += contains(b, nb, a[i]);
+    return c;
+}
+
+/* A n B, sorted, for sorted A, B */
+static int intersect(const int32_t *a, int64_t na, const int32_t *b, int64_t nb, ovec *out)
+{
+    if (na > nb) {
+        const int32_t *t = a;
+        a = b;
+        b = t;
+        int64_t tn = na;
+        na = nb;
+        nb = tn;
+    }
+    for (int64_t i = 0; i < na; ++i)
+        if (contains(b, nb, a[i]) && ov_push(out, a[i])) return -1;
+    return 0;
+}
+
+/* ----------------------------------------------------------- accumulator */
+
+typedef struct {
+    uint64_t count, hash, nodes;
+    uint64_t bytes; /* algorithmic bytes, see bytes_node / bytes_root */
+    ovec *records;  /* optional: per biclique |R|, |L|, R sorted, L sorted */
+    int err;
+} oacc;
+
+/*
+ * Algorithmic bytes (the roofline numerator). Below the top level every
+ * candidate row is the bit pattern of N(y) n L packed in 64-bit words, so a
+ * node of a call with level set L reads ceil(|L|/64) words for x's row and
+ * for every row it tests: all of Q (the check reads it to the end unless it
+ * rejects; counted in full) and, when the node is maximal, the rest of P.
+ * A top-level node instead reads the adjacency that builds the root's local
+ * universe: N(r) and N(w) for every w in N(r), int32 each.
+ */
+static uint64_t bytes_node(int64_t nL, int64_t nQ, int64_t n_rest, int maximal)
+{
+    uint64_t words = (uint64_t)((nL + 63) / 64);
+    return 8ULL * words * (uint64_t)(1 + nQ + (maximal ? n_rest : 0));
+}
+
+static void emit(oacc *acc, const ovec *L, const ovec *R)
+{
+    uint64_t s = 0;
+    for (int64_t i = 0; i < R->n; ++i) s += key_u(R->a[i]);
+    for (int64_t i = 0; i < L->n; ++i) s += key_v(L->a[i]);
+    acc->count += 1;
+    acc->hash += orc_sm(s);
+    if (acc->records) {
+        int32_t *rs = (int32_t *)malloc((size_t)(R->n ? R->n : 1) * sizeof(int32_t));
+        if (!rs) {
+            acc->err = 1;
+            return;
+        }
+        memcpy(rs, R->a, (size_t)R->n * sizeof(int32_t));
+        qsort(rs, (size_t)R->n, sizeof(int32_t), cmp_i32);
+        int bad = ov_push(acc->records, (int32_t)R->n) || ov_push(acc->records, (int32_t)L->n);
+        for (int64_t i = 0; i < R->n; ++i) bad |= ov_push(acc->records, rs[i]);
+        for (int64_t i = 0; i < L->n; ++i) bad |= ov_push(acc->records, L->a[i]);
+        free(rs);
+        if (bad) acc->err = 1;
+    }
+}
+
+/* ------------------------------------------------------------ Algorithm 1 */
+
+static void mbea(const ograph *g, const ovec *L, const ovec *R, const ovec *P, const ovec *Q, oacc *acc);
+
+/*
+ * One iteration of Algorithm 1's while loop with candidate x already popped:
+ * P_rest is P after the pop, Q the current maximality-checking set.
+ */
+static void mbea_iteration(const ograph *g, const ovec *L, const ovec *R, int32_t x, const int32_t *P_rest,
+                           int64_t n_rest, const int32_t *Q, int64_t nQ, oacc *acc)
+{
+    ovec Rp = {0}, Lp = {0}, Pp = {0}, Qp = {0};
+    int64_t dx;
+    const int32_t *Nx = nbr(g, x, &dx);
+    acc->nodes += 1;
+
+    /* Step 1: R' = R u {x} */
+    for (int64_t i = 0; i < R->n; ++i)
+        if (ov_push(&Rp, R->a[i])) goto oom;
+    if (ov_push(&Rp, x)) goto oom;
+
+    /* Step 2: L' = { v in L : (x, v) in E } */
+    if (intersect(L->a, L->n, Nx, dx, &Lp)) goto oom;
+
+    /* Step 3: maximality check against Q */
+    int is_maximal = 1;
+    for (int64_t i = 0; i < nQ; ++i) {
+        int64_t dq;
+        const int32_t *Nq = nbr(g, Q[i], &dq);
+        int64_t c = count_common(Nq, dq, Lp.a, Lp.n);
+        if (c == Lp.n) {
+            is_maximal = 0;
+            break;
+        } else if (c > 0) {
+            if (ov_push(&Qp, Q[i])) goto oom;
+        }
+    }
+
+    if (is_maximal) {
+        /* Step 4: maximal expansion over the rest of P */
+        for (int64_t i = 0; i < n_rest; ++i) {
+            int64_t dp;
+            const int32_t *Np = nbr(g, P_rest[i], &dp);
+            int64_t c = count_common(Np, dp, Lp.a, Lp.n);
+            if (c == Lp.n) {
+                if (ov_push(&Rp, P_rest[i])) goto oom;
+            } else if (c > 0) {
+                if (ov_push(&Pp, P_rest[i])) goto oom;
+            }
+        }
+        emit(acc, &Lp, &Rp);
+        if (Pp.n != 0) mbea(g, &Lp, &Rp, &Pp, &Qp, acc);
+    }
+    if (R->n == 0) { /* top level: the root's adjacency */
+        uint64_t b = 4ULL * (uint64_t)dx;
+        for (int64_t k = 0; k < dx; ++k) b += 4ULL * (uint64_t)(g->v_off[Nx[k] + 1] - g->v_off[Nx[k]]);
+        acc->bytes += b;
+    } else {
+        acc->bytes += bytes_node(L->n, nQ, n_rest, is_maximal);
+    }
+    goto done;
+oom:
+    acc->err = 1;
+done:
+    ov_free(&Rp);
+    ov_free(&Lp);
+    ov_free(&Pp);
+    ov_free(&Qp);
+}
+
+typedef struct {
+    int64_t key;
+    int32_t id;
+} okey;
+
+static int cmp_key(const void *a, const void *b)
+{
+    const okey *x = (const okey *)a, *y = (const okey *)b;
+    if (x->key != y->key) return (x->key > y->key) - (x->key < y->key);
+    return (x->id > y->id) - (x->id < y->id);
+}
+
+/* Algorithm 1: MBEA(L, R, P, Q) */
+static void mbea(const ograph *g, const ovec *L, const ovec *R, const ovec *P, const ovec *Q, oacc *acc)
+{
+    int64_t nP = P->n;
+    okey *ord = (okey *)malloc((size_t)(nP ? nP : 1) * sizeof(okey));
+    int32_t *seq = (int32_t *)malloc((size_t)(nP ? nP : 1) * sizeof(int32_t));
+    ovec Qc = {0};
+    if (!ord || !seq) goto oom;
+    /* candidate selection key |N(v) n L|, then id */
+    for (int64_t i = 0; i < nP; ++i) {
+        int64_t dv;
+        const int32_t *Nv = nbr(g, P->a[i], &dv);
+        ord[i].key = count_common(Nv, dv, L->a, L->n);
+        ord[i].id = P->a[i];
+    }
+    qsort(ord, (size_t)nP, sizeof(okey), cmp_key);
+    for (int64_t i = 0; i < nP; ++i) seq[i] = ord[i].id;
+    for (int64_t i = 0; i < Q->n; ++i)
+        if (ov_push(&Qc, Q->a[i])) goto oom;
+
+    for (int64_t i = 0; i < nP && !acc->err; ++i) { /* while |P| > 0 */
+        int32_t x = seq[i];                         /* x = P.pop() */
+        mbea_iteration(g, L, R, x, seq + i + 1, nP - i - 1, Qc.a, Qc.n, acc);
+        if (ov_push(&Qc, x)) goto oom; /* Q = Q u {x} */
+    }
+    goto done;
+oom:
+    acc->err = 1;
+done:
+    free(ord);
+    free(seq);
+    ov_free(&Qc);
+}
+
+/* Initial sets of the top-level call. */
+static int top_level(const ograph *g, ovec *L, ovec *P)
+{
+    for (int32_t v = 0; v < g->nV; ++v)
+        if (ov_push(L, v)) return -1;
+    for (int32_t u = 0; u < g->nU; ++u)
+        if (g->u_off[u + 1] > g->u_off[u] && ov_push(P, u)) return -1;
+    return 0;
+}
+
+/*
+ * Whole-graph enumeration, serial. out[0..3] = count, hash, nodes, bytes.
+ * When rec != NULL, *rec receives a malloc'd int32 array of records
+ * (|R|, |L|, R..., L...) and *rec_len its length (free with orc_free).
+ * Returns 0, or -1 on allocation failure.
+ */
+int orc_enumerate(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
+                  const int32_t *v_adj, uint64_t *out, int32_t **rec, int64_t *rec_len)
+{
+    ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
+    ovec L = {0}, R = {0}, P = {0}, Q = {0}, records = {0};
+    oacc acc = {0, 0, 0, 0, rec ? &records : NULL, 0};
+    if (top_level(&g, &L, &P)) acc.err = 1;
+    else mbea(&g, &L, &R, &P, &Q, &acc);
+    ov_free(&L);
+    ov_free(&P);
+    out[0] = acc.count;
+    out[1] = acc.hash;
+    out[2] = acc.nodes;
+    out[3] = acc.bytes;
+    if (rec) {
+        *rec = records.a;
+        *rec_len = records.n;
+    } else {
+        ov_free(&records);
+    }
+    return acc.err ? -1 : 0;
+}
+
+void orc_free(void *p) { free(p); }
+
+/* ------------------------------------------------------ per-root driver */
+/*
+ * The i-th iteration of the top-level while loop depends only on the
+ * top-level pop sequence: x = seq[i], P after the pop = seq[i+1..],
+ * Q = seq[0..i). So each top-level iteration ("root") can be run on its
+ * own, and the per-root results of all roots add up to the whole run.
+ */
+
+typedef struct {
+    const ograph *g;
+    const int32_t *seq;
+    const int64_t *pos;
+    int64_t nseq;
+    const ovec *L;
+    const int32_t *roots;
+    int64_t nroots;
+    uint64_t *out;
+    int64_t next;
+    pthread_mutex_t mu;
+    int err;
+} root_job;
+
+static void run_root(root_job *j, int64_t k)
+{
+    int32_t r = j->roots[k];
+    uint64_t *o = j->out + 4 * k;
+    o[0] = o[1] = o[2] = o[3] = 0;
+    if (r < 0 || r >= j->g->nU || j->pos[r] < 0) return; /* isolated: never popped */
+    int64_t i = j->pos[r];
+    ovec R = {0};
+    oacc acc = {0, 0, 0, 0, NULL, 0};
+    mbea_iteration(j->g, j->L, &R, r, j->seq + i + 1, j->nseq - i - 1, j->seq, i, &acc);
+    o[0] = acc.count;
+    o[1] = acc.hash;
+    o[2] = acc.nodes;
+    o[3] = acc.bytes;
+    if (acc.err) j->err = 1;
+}
+
+static void *root_worker(void *arg)
+{
+    root_job *j = (root_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        int64_t k = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (k >= j->nroots) break;
+        run_root(j, k);
+    }
+    return NULL;
+}
+
+/*
+ * Per-root results: out[4k..4k+3] = (count, hash, nodes, bytes) of the top-level
+ * iteration whose candidate is roots[k] (zeros for an isolated vertex).
+ * Runs on nthreads POSIX threads. Returns 0 or -1.
+ */
+int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
+                 const int32_t *v_adj, const int32_t *roots, int64_t nroots, uint64_t *out, int32_t nthreads)
+{
+    ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
+    ovec L = {0}, P = {0};
+    int rc = -1;
+    okey *ord = NULL;
+    int32_t *seq = NULL;
+    int64_t *pos = NULL;
+    if (top_level(&g, &L, &P)) goto done;
+    ord = (okey *)malloc((size_t)(P.n ? P.n : 1) * sizeof(okey));
+    seq = (int32_t *)malloc((size_t)(P.n ? P.n : 1) * sizeof(int32_t));
+    pos = (int64_t *)malloc((size_t)(nU ? nU : 1) * sizeof(int64_t));
+    if (!ord || !seq || !pos) goto done;
+    /* the same top-level pop sequence as mbea(): (|N(u) n V|, id) */
+    for (int64_t i = 0; i < P.n; ++i) {
+        int64_t du;
+        const int32_t *Nu = nbr(&g, P.a[i], &du);
+        ord[i].key = count_common(Nu, du, L.a, L.n);
+        ord[i].id = P.a[i];
+    }
+    qsort(ord, (size_t)P.n, sizeof(okey), cmp_key);
+    for (int32_t u = 0; u < nU; ++u) pos[u] = -1;
+    for (int64_t i = 0; i < P.n; ++i) {
+        seq[i] = ord[i].id;
+        pos[seq[i]] = i;
+    }
+    root_job job;
+    job.g = &g;
+    job.seq = seq;
+    job.pos = pos;
+    job.nseq = P.n;
+    job.L = &L;
+    job.roots = roots;
+    job.nroots = nroots;
+    job.out = out;
+    job.next = 0;
+    job.err = 0;
+    pthread_mutex_init(&job.mu, NULL);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads == 1) {
+        root_worker(&job);
+    } else {
+        pthread_t *th = (pthread_t *)malloc((size_t)nthreads * sizeof(pthread_t));
+        int started = 0;
+        for (int t = 0; t < nthreads && th; ++t)
+            if (pthread_create(&th[t], NULL, root_worker, &job) == 0) started++;
+        if (started == 0) root_worker(&job);
+        for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+        free(th);
+    }
+    pthread_mutex_destroy(&job.mu);
+    rc = job.err ? -1 : 0;
+done:
+    ov_free(&L);
+    ov_free(&P);
+    free(ord);
+    free(seq);
+    free(pos);
+    return rc;
+}
+
+/* The top-level pop sequence (non-isolated U sorted by (degree, id)). */
+int orc_root_order(int32_t nU, const int32_t *u_off, int32_t *seq_out, int64_t *n_out)
+{
+    okey *ord = (okey *)malloc((size_t)(nU ? nU : 1) * sizeof(okey));
+    if (!ord) return -1;
+    int64_t n = 0;
+    for (int32_t u = 0; u < nU; ++u) {
+        int64_t d = u_off[u + 1] - u_off[u];
+        if (d > 0) {
+            ord[n].key = d;
+            ord[n].id = u;
+            n++;
+        }
+    }
+    qsort(ord, (size_t)n, sizeof(okey), cmp_key);
+    for (int64_t i = 0; i < n; ++i) seq_out[i] = ord[i].id;
+    *n_out = n;
+    free(ord);
+    return 0;
+}
+
+/* ------------------------------------------------------ many-graph driver */
+
+typedef struct {
+    int32_t n_graphs;
+    const int32_t *nU, *nV;
+    const int64_t *edge_off, *u_off_start, *v_off_start;
+    const int32_t *u_off, *u_adj, *v_off, *v_adj;
+    const int32_t *order;
+    uint64_t *out;
+    int64_t next;
+    pthread_mutex_t mu;
+    int err;
+} batch_job;
+
+static void *batch_worker(void *arg)
+{
+    batch_job *j = (batch_job *)arg;
+    for (;;) {
+        pthread_mutex_lock(&j->mu);
+        int64_t k = j->next++;
+        pthread_mutex_unlock(&j->mu);
+        if (k >= j->n_graphs) break;
+        int32_t gi = j->order ? j->order[k] : (int32_t)k;
+        int64_t e0 = j->edge_off[gi];
+        const int32_t *uo = j->u_off + j->u_off_start[gi];
+        const int32_t *vo = j->v_off + j->v_off_start[gi];
+        if (orc_enumerate(j->nU[gi], j->nV[gi], uo, j->u_adj + e0, vo, j->v_adj + e0, j->out + 4 * (int64_t)gi,
+                          NULL, NULL))
+            j->err = 1;
+    }
+    return NULL;
+}
+
+/*
+ * Many independent graphs (concatenated CSR/CSC, per-graph local offsets).
+ * out[4g..4g+3] = (count, hash, nodes, bytes) of graph g. order (optional) is the
+ * sequence in which threads pick graphs up. Returns 0 or -1.
+ */
+int orc_batch(int32_t n_graphs, const int32_t *nU, const int32_t *nV, const int64_t *edge_off,
+              const int64_t *u_off_start, const int64_t *v_off_start, const int32_t *u_off,
+              const int32_t *u_adj, const int32_t *v_off, const int32_t *v_adj, const int32_t *order,
+              uint64_t *out, int32_t nthreads)
+{
+    batch_job job = {n_graphs, nU, nV, edge_off, u_off_start, v_off_start, u_off, u_adj, v_off, v_adj,
+                     order, out, 0};
+    job.err = 0;
+    pthread_mutex_init(&job.mu, NULL);
+    if (nthreads < 1) nthreads = 1;
+    pthread_t *th = (pthread_t *)malloc((size_t)nthreads * sizeof(pthread_t));
+    int started = 0;
+    for (int t = 0; t < nthreads && th; ++t)
+        if (pthread_create(&th[t], NULL, batch_worker, &job) == 0) started++;
+    if (started == 0) batch_worker(&job);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&job.mu);
+    return job.err ? -1 : 0;
+}
+
+/* ---------------------------------------------------------- brute force */
+/*
+ * Independent second oracle straight from the definition: for every
+ * nonempty A subset of U (|U| <= 24), B = Gamma(A); keep (A, B) when B is
+ * nonempty and Gamma(B) = A. Sets are 64-bit word bitsets over V.
+ * out[0..1] = count, hash; records as in orc_enumerate.
+ */
+int orc_bruteforce(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, uint64_t *out,
+                   int32_t **rec, int64_t *rec_len)
+{
+    if (nU > 24 || nU < 0) return -1;
+    int64_t W = (nV + 63) / 64;
+    uint64_t *rows = (uint64_t *)calloc((size_t)(nU ? nU : 1) * (size_t)(W ? W : 1), sizeof(uint64_t));
+    uint64_t *B = (uint64_t *)malloc((size_t)(W ? W : 1) * sizeof(uint64_t));
+    ovec records = {0};
+    int err = 0;
+    if (!rows || !B) {
+        free(rows);
+        free(B);
+        return -1;
+    }
+    for (int32_t u = 0; u < nU; ++u)
+        for (int32_t k = u_off[u]; k < u_off[u + 1]; ++k) rows[(int64_t)u * W + u_adj[k] / 64] |= 1ULL << (u_adj[k] % 64);
+    uint64_t count = 0, hash = 0;
+    for (uint64_t mask = 1; mask < (1ULL << nU); ++mask) {
+        for (int64_t w = 0; w < W; ++w) B[w] = ~0ULL;
+        if (nV % 64 && W) B[W - 1] = (1ULL << (nV % 64)) - 1;
+        for (int32_t u = 0; u < nU; ++u)
+            if (mask >> u & 1)
+                for (int64_t w = 0; w < W; ++w) B[w] &= rows[(int64_t)u * W + w];
+        int nonempty = 0;
+        for (int64_t w = 0; w < W; ++w) nonempty |= (B[w] != 0);
+        if (!nonempty) continue;
+        uint64_t closure = 0; /* Gamma(B) as a mask over U */
+        for (int32_t u = 0; u < nU; ++u) {
+            int sup = 1;
+            for (int64_t w = 0; w < W; ++w) sup &= ((rows[(int64_t)u * W + w] & B[w]) == B[w]);
+            if (sup) closure |= 1ULL << u;
+        }
+        if (closure != mask) continue;
+        uint64_t s = 0;
+        int32_t na = 0, nb = 0;
+        for (int32_t u = 0; u < nU; ++u)
+            if (mask >> u & 1) {
+                s += key_u(u);
+                na++;
+            }
+        for (int32_t v = 0; v < nV; ++v)
+            if (B[v / 64] >> (v % 64) & 1) {
+                s += key_v(v);
+                nb++;
+            }
+        count++;
+        hash += orc_sm(s);
+        if (rec) {
+            err |= ov_push(&records, na) | ov_push(&records, nb);
+            for (int32_t u = 0; u < nU; ++u)
+                if (mask >> u & 1) err |= ov_push(&records, u);
+            for (int32_t v = 0; v < nV; ++v)
+                if (B[v / 64] >> (v % 64) & 1) err |= ov_push(&records, v);
+        }
+    }
+    free(rows);
+    free(B);
+    out[0] = count;
+    out[1] = hash;
+    if (rec) {
+        *rec = records.a;
+        *rec_len = records.n;
+    } else {
+        ov_free(&records);
+    }
+    return err ? -1 : 0;
+}
