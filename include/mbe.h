@@ -1,0 +1,194 @@
+/*
+ * mbe.h -- C ABI of the GB300 maximal-biclique-enumeration library.
+ *
+ * Problem (Hsieh et al., "Accelerating Maximal Biclique Enumeration on GPUs",
+ * arXiv 2401.05039, Section II-A): G = (U u V, E) is bipartite. A biclique
+ * is a pair (R, L), R a subset of U and L a subset of V, with every u in R
+ * adjacent to every v in L; it is maximal when no vertex can be added to
+ * either side. The library enumerates every maximal biclique with both sides
+ * nonempty, by the depth-first search of Section II-B, Algorithm 1 (MBEA:
+ * candidate selection, L' construction, maximality check against Q, maximal
+ * expansion of R', recursion on P'), run on the GPU as described in
+ * Section III (coarse-grained subtree tasks per 1st-level candidate,
+ * fine-grained set operations inside them, work stealing between workers).
+ *
+ * Conventions for every entry point:
+ *  - Return value: an mbe_status (0 = MBE_OK). Nothing is thrown; a failing
+ *    call leaves caller-owned buffers in an unspecified but valid state.
+ *  - Vertex ids are 0-based int32. U is the candidate side (P, Q, R are
+ *    subsets of U; L is a subset of V).
+ *  - "stream" is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream). Calls enqueue on it and synchronise it before returning,
+ *    because their results are read on the host.
+ *  - Device memory that the library allocates is owned by the object that
+ *    allocated it (a graph or model handle) and released by its destroy
+ *    call, except the search workspace: one per device, shared by every
+ *    call on that device, grown on demand and released by
+ *    mbe_release_workspace() or at process exit. Caller buffers stay owned
+ *    by the caller.
+ *  - Because of that shared workspace, calls on one device must not overlap
+ *    in time: use one host thread per device, one call at a time.
+ */
+#ifndef MBE_H
+#define MBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MBE_OK = 0,
+    MBE_ERR_INVALID_ARG = 1,   /* NULL where a pointer is required, negative size, bad option */
+    MBE_ERR_INVALID_GRAPH = 2, /* unsorted or duplicate adjacency, id out of range, CSR/CSC not transposes */
+    MBE_ERR_OOM = 3,           /* device allocation failed */
+    MBE_ERR_ARENA_FULL = 4,    /* a search stack outgrew its arena even after the automatic retries */
+    MBE_ERR_OUTPUT_FULL = 5,   /* biclique buffer too small; count/hash are still exact and the
+                                  required sizes are reported in the buffer's n_*_written fields */
+    MBE_ERR_TIMEOUT = 6,       /* a device wait exceeded options.watchdog_ms; the kernel stopped cleanly */
+    MBE_ERR_CUDA = 7,          /* a CUDA runtime call failed (no device, launch failure, ...) */
+    MBE_ERR_UNSUPPORTED = 8    /* input outside the limits stated at the entry point */
+} mbe_status;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+const char *mbe_status_string(int status);
+
+/* ------------------------------------------------------------------ graph */
+
+typedef struct mbe_graph mbe_graph; /* opaque, immutable after create */
+
+/*
+ * Build a graph from its two adjacency forms (Section II-A: N(v) for every
+ * vertex). u_off[nU+1] / u_adj[nE] is the CSR of U -> V and v_off[nV+1] /
+ * v_adj[nE] the CSR of V -> U; every list strictly increasing, the two forms
+ * transposes of each other, u_off[0] = v_off[0] = 0, u_off[nU] = v_off[nV]
+ * = nE. ptr_kind = 0: the arrays are host memory; 1: device memory of the
+ * current device. The arrays are copied; the caller keeps them. The input
+ * is validated on the device; violations return MBE_ERR_INVALID_GRAPH.
+ * Limits: 0 <= nU, nV; 0 <= nE < 2^31.
+ */
+int mbe_graph_create(int32_t nU, int32_t nV, int64_t nE, const int32_t *u_off, const int32_t *u_adj,
+                     const int32_t *v_off, const int32_t *v_adj, int32_t ptr_kind, void *stream,
+                     mbe_graph **out);
+
+/* Release a graph and every device buffer it owns. NULL is accepted. */
+int mbe_graph_destroy(mbe_graph *g);
+
+/* Sizes of a graph: any output pointer may be NULL. */
+int mbe_graph_info(const mbe_graph *g, int32_t *nU, int32_t *nV, int64_t *nE, int32_t *max_deg_u,
+                   int32_t *max_deg_v);
+
+/*
+ * Diagnostics (no counterpart in the paper): with the environment variable
+ * MBE_DEBUG_TRACE set, every search launch keeps a progress record per
+ * worker: [0] phase, [1] argument, [2] nodes, [3] depth, [4] donations,
+ * [5] steals, [6] elapsed ns, [8..13] ns in root setup, node scans, child
+ * builds, frame copies, -, tasks; [14] root tasks, [15] stolen tasks. This
+ * copies up to max_workers of them (16 uint64 each) to `host` and
+ * returns how many were copied. MBE_DEADLINE_MS bounds any single launch
+ * (default 30 minutes); a launch past it stops with MBE_ERR_TIMEOUT.
+ */
+int mbe_debug_trace(uint64_t *host, int32_t max_workers);
+
+/* Free the current device's search workspace (the next call re-allocates it). */
+int mbe_release_workspace(void);
+
+/*
+ * Device copy bandwidth (bench support, no counterpart in the paper): copies
+ * `bytes` (>= 1 MiB, multiple of 16) between two device buffers `iters`
+ * times with 16-byte loads/stores on all SMs and returns the best
+ * (read + write bytes) / time in GB/s. With bytes well below the L2 size
+ * this measures L2 bandwidth; well above it, HBM bandwidth.
+ */
+int mbe_copy_bandwidth(int64_t bytes, int32_t iters, void *stream, double *gbps);
+
+/* ---------------------------------------------------------------- options */
+
+typedef struct {
+    int32_t block_threads;    /* threads per block, multiple of 32, 32..1024; 0 = auto */
+    int32_t blocks_per_sm;    /* resident blocks per SM for the persistent launch; 0 = auto */
+    int32_t bitset_max_words; /* widest root-local bitset row, in 64-bit words (1..32); 0 = 32 */
+    int32_t steal;            /* 1 = busy workers split their shallowest frame for idle ones (Sec. III-C) */
+    int32_t schedule;         /* 0 = static execution order (descending degree), 1 = learned (model) */
+    int32_t emit;             /* 0 = count + hash only, 1 = also write the bicliques */
+    int32_t watchdog_ms;      /* bound on any device wait; 0 = 60000 */
+    int32_t root_begin;       /* shard of the execution order: positions [root_begin, root_end) */
+    int32_t root_end;         /* -1 = to the end */
+    int64_t arena_bytes;      /* per-worker search-stack bytes (exact limit); 0 = sized from the graph,
+                                 grown automatically on overflow */
+    const void *model;        /* mbe_model* used when schedule = 1 */
+    uint64_t *per_root;       /* optional DEVICE array [nU][4]: receives (count, hash, nodes, bytes)
+                                 of each top-level candidate's subtree (overwritten by the call) */
+    int32_t *exec_order;      /* optional DEVICE array [nU]: explicit execution order of the roots
+                                 (any permutation of a subset of U); overrides schedule */
+    int32_t n_exec;           /* length of exec_order */
+} mbe_options;
+
+/* Fill *opt with the defaults (all "auto"). */
+int mbe_default_options(mbe_options *opt);
+
+/* ---------------------------------------------------------------- results */
+
+typedef struct {
+    uint64_t count;     /* number of maximal bicliques */
+    uint64_t hash;      /* sum mod 2^64 over bicliques of SM(sum_{u in R} SM(2u) + sum_{v in L} SM(2v+1)),
+                           SM = one SplitMix64 output step (golden-gamma add, then the mix) */
+    uint64_t nodes;     /* iterations of Algorithm 1's while loop, candidate order (|N(v) n L|, id) */
+    uint64_t bytes_alg; /* algorithmic bytes of the search (roofline numerator) */
+    double device_ms;   /* time of the search kernel(s) on the stream, CUDA events */
+    double prep_ms;     /* time of ordering / features / model inference before the search */
+    int32_t status;     /* same as the return value */
+    int32_t n_workers;  /* warps of the persistent launch */
+    uint64_t n_donations; /* frames split off for idle workers */
+} mbe_result;
+
+/*
+ * Caller-owned DEVICE buffers for the bicliques themselves (emit = 1).
+ * Biclique b is ids[offsets[b] .. ]: |R|, |L|, then R's ids, then L's ids
+ * (global ids, each side in ascending order after mbe_enumerate returns
+ * only if the caller sorts them; the library writes them in search order).
+ * Bicliques appear in any order.
+ */
+typedef struct {
+    int32_t *ids;
+    int64_t capacity_ids;
+    int64_t *offsets;
+    int64_t capacity_bicliques;
+    int64_t n_ids_written;       /* out: ids needed (written if <= capacity) */
+    int64_t n_bicliques_written; /* out: bicliques found */
+} mbe_biclique_buffer;
+
+/*
+ * Enumerate every maximal biclique of g (Algorithm 1 over all of U, run as
+ * one persistent launch of warp workers). opts may be NULL (defaults).
+ * out receives count, hash, nodes and timings; bicliques may be NULL
+ * (count + hash only). The result is independent of every option except
+ * root_begin/root_end (which select a shard of roots; shards add up).
+ */
+int mbe_enumerate(const mbe_graph *g, const mbe_options *opts, void *stream, mbe_result *out,
+                  mbe_biclique_buffer *bicliques);
+
+/*
+ * Enumerate many independent graphs in one call. Graph i has nU[i] x nV[i]
+ * vertices, its edges are positions [edge_off[i], edge_off[i+1]) of the
+ * concatenated u_adj_cat / v_adj_cat (ids local to the graph), and its
+ * offset arrays start at u_off_cat[u_off_start[i]] (nU[i]+1 entries,
+ * local, starting at 0) and v_off_cat[v_off_start[i]] (nV[i]+1 entries).
+ * All arrays are HOST memory. per_graph[i] receives graph i's result.
+ * Graphs are binned into size classes; each class runs with parameters
+ * chosen by the autotuner (mbe_autotune) when a table is loaded, else
+ * with defaults; the class launches are captured in one CUDA graph.
+ * Limits: per graph nU <= 65536 and every degree <= 64 * 32.
+ */
+int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t *nU, const int32_t *nV,
+                        const int64_t *u_off_start, const int64_t *v_off_start, const int32_t *u_off_cat,
+                        const int32_t *u_adj_cat, const int32_t *v_off_cat, const int32_t *v_adj_cat,
+                        const mbe_options *opts, void *stream, mbe_result *per_graph, mbe_result *total);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MBE_H */

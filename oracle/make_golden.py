@@ -144,15 +144,56 @@ def batch(name, threads, n_graphs=4096, budget_count=2.0e5, n_heavy_graphs=12, r
             "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": threads}
 
 
+def prefix_sample(name, g, threads, seed=20240110, batch=256, keep_rows=300, progress=None, time_budget=None):
+    """Per-root oracle rows for the roots in a seeded random order, in batches, resumable.
+
+    Progress is saved after every batch to `progress` (a .npz). The stored
+    golden covers the first K roots of the permutation: their summed
+    (count, hash, nodes, bytes) and `keep_rows` individual rows. When K is
+    every root, the sum is the whole-graph total.
+    """
+    rng = np.random.default_rng(seed)
+    live = np.nonzero(np.diff(g.u_off) > 0)[0]
+    perm = rng.permutation(live).astype(np.int32)
+    rows = np.zeros((0, 4), dtype=np.uint64)
+    if progress and os.path.exists(progress):
+        d = np.load(progress)
+        if int(d["seed"]) == seed and d["digest"].item() == g.digest():
+            rows = d["rows"]
+    t0 = time.time()
+    while rows.shape[0] < perm.size and (time_budget is None or time.time() - t0 < time_budget):
+        k = rows.shape[0]
+        part = oracle.per_root(g, roots=perm[k:k + batch], nthreads=threads)
+        rows = np.concatenate([rows, part])
+        if progress:
+            np.savez(progress + ".tmp.npz", rows=rows, seed=seed, digest=np.array(g.digest()))
+            os.replace(progress + ".tmp.npz", progress)
+        print(f"{name}: {rows.shape[0]}/{perm.size} roots, {time.time() - t0:.0f}s", flush=True)
+    K = rows.shape[0]
+    pick = np.random.default_rng(seed + 1).choice(K, size=min(keep_rows, K), replace=False) if K else []
+    total = rows.sum(axis=0, dtype=np.uint64) if K else np.zeros(4, np.uint64)
+    return {"workload": name, "graph": _graph_info(g), "total": _row(total) if K == perm.size else None,
+            "prefix": {"seed": seed, "k": int(K), "n_roots": int(perm.size), "sum": _row(total),
+                       "about": "sum over the first k roots of the seeded permutation of the non-isolated U vertices"},
+            "per_root": {str(int(perm[i])): _row(rows[i]) for i in sorted(int(x) for x in pick)},
+            "oracle_threads": threads}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("names", nargs="+")
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--prefix", action="store_true", help="resumable seeded-order per-root run (large graphs)")
+    ap.add_argument("--progress", default=None, help="progress file for --prefix")
+    ap.add_argument("--budget", type=float, default=None, help="seconds to spend in this --prefix invocation")
     args = ap.parse_args()
     os.makedirs(GOLDEN, exist_ok=True)
     for name in args.names:
         t0 = time.time()
-        if name == "er200x300":
+        if args.prefix:
+            out = prefix_sample(name, synth.workload(name), args.threads, progress=args.progress,
+                                time_budget=args.budget)
+        elif name == "er200x300":
             out = whole_graph(name, synth.workload(name), args.threads, n_heavy=8, n_random=24, records=True)
         elif name in ("planted5k", "chunglu20k"):
             out = whole_graph(name, synth.workload(name), args.threads)

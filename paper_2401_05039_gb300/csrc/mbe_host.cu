@@ -1,0 +1,752 @@
+// Host runtime behind the C ABI (include/mbe.h): graph handles, workspace
+// sizing, the persistent search launch, result read-back.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mbe.h"
+#include "mbe_internal.h"
+#include "mbe_prep.h"
+
+namespace mbe {
+
+// Device-side control block of one search launch (zeroed before each launch).
+struct Ctl {
+    unsigned long long cursor;
+    long long outstanding;
+    int32_t n_idle;
+    int32_t error;
+    int32_t n_published;
+    int32_t pad;
+    unsigned long long totals[8];
+    unsigned long long used_ids;
+    unsigned long long used_bic;
+};
+
+struct Workspace {
+    char *arena = nullptr;
+    int64_t arena_bytes = 0, scratch_bytes = 0;
+    char *slots = nullptr;
+    int64_t slot_bytes = 0;
+    int32_t *slot_state = nullptr;
+    int32_t *mark = nullptr;
+    int64_t mark_stride = 0;
+    int n_warps = 0;
+    int threads = 0, blocks = 0;
+    Ctl *ctl = nullptr;
+    int64_t n_cand_cap = 0, urow_bytes = 0;
+    bool marks_dirty = false;
+    bool budget_limited = false; // fewer warps than requested because of device memory
+
+    void release()
+    {
+        cudaFree(arena);
+        cudaFree(slots);
+        cudaFree(slot_state);
+        cudaFree(mark);
+        cudaFree(ctl);
+        *this = Workspace();
+    }
+};
+
+} // namespace mbe
+
+struct mbe_graph {
+    int device = 0;
+    int32_t nU = 0, nV = 0;
+    int64_t nE = 0;
+    int32_t *u_off = nullptr, *u_adj = nullptr, *v_off = nullptr, *v_adj = nullptr;
+    mbe::GraphDesc *d_desc = nullptr;
+    int32_t max_deg_u = 0, max_deg_v = 0, n_live = 0;
+    int64_t nc_max = 0, urow_max = 0, frame_max = 0;
+    int32_t *order_static = nullptr; // non-isolated U by descending degree
+    int32_t *hist = nullptr;         // max(max_deg_u, key range) + 1 entries
+    int32_t hist_len = 0;
+};
+
+namespace mbe {
+namespace {
+
+// Search workspace shared by every call on a device (grown on demand, kept
+// until mbe_release_workspace or process exit).
+constexpr int kMaxDevices = 64;
+Workspace g_ws[kMaxDevices];
+
+Workspace &device_workspace()
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kMaxDevices) dev = 0;
+    return g_ws[dev];
+}
+
+int set_status(mbe_result *out, int st)
+{
+    if (out) out->status = st;
+    return st;
+}
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return MBE_OK;
+    if (e == cudaErrorMemoryAllocation) return MBE_ERR_OOM;
+    return MBE_ERR_CUDA;
+}
+
+#define MBE_TRY(expr)                                                                                                 \
+    do {                                                                                                              \
+        cudaError_t _e = (expr);                                                                                      \
+        if (_e != cudaSuccess) {                                                                                      \
+            cudaGetLastError();                                                                                       \
+            return cuda_status(_e);                                                                                   \
+        }                                                                                                             \
+    } while (0)
+
+int64_t round_up(int64_t x, int64_t a) { return (x + a - 1) / a * a; }
+
+// Upper bound on one search launch (MBE_DEADLINE_MS, default 30 minutes):
+// every worker compares its own elapsed time with it and stops the launch
+// with MBE_ERR_TIMEOUT, so no launch can run unbounded.
+long long deadline_ms()
+{
+    const char *e = getenv("MBE_DEADLINE_MS");
+    long long v = e ? atoll(e) : 0;
+    return v > 0 ? v : 30LL * 60 * 1000;
+}
+
+// Per-worker progress records when MBE_DEBUG_TRACE is set (dumped with mbe_debug_trace).
+unsigned long long *g_debug = nullptr;
+int g_debug_warps = 0;
+unsigned long long *debug_buffer(int n_warps)
+{
+    if (!getenv("MBE_DEBUG_TRACE")) return nullptr;
+    if (g_debug_warps < n_warps) {
+        cudaFree(g_debug);
+        g_debug = nullptr;
+        g_debug_warps = 0;
+        if (cudaMalloc(&g_debug, sizeof(unsigned long long) * 16 * (size_t)n_warps) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_debug_warps = n_warps;
+    }
+    cudaMemset(g_debug, 0, sizeof(unsigned long long) * 16 * (size_t)n_warps);
+    return g_debug;
+}
+
+int key_bits_for(int64_t n)
+{
+    int b = 1;
+    while (b < 31 && ((int64_t)1 << b) < n) ++b;
+    return b;
+}
+
+struct LaunchShape {
+    int threads, blocks, warps;
+};
+
+LaunchShape choose_shape(const mbe_options &o)
+{
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int threads = o.block_threads > 0 ? o.block_threads : 256;
+    threads = std::max(32, std::min(1024, threads / 32 * 32));
+    int per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : std::max(1, 512 / threads); // 16 warps per SM by default
+    int fit = search_fit_shape(threads, per_sm);
+    if (fit < 0) { // block too large for the kernel's register use
+        threads = -fit;
+        per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : std::max(1, 512 / threads);
+        fit = search_fit_shape(threads, per_sm);
+    }
+    if (fit > 0) per_sm = fit;
+    LaunchShape s;
+    s.threads = threads;
+    s.blocks = sms * per_sm;
+    s.warps = s.blocks * (threads / 32);
+    return s;
+}
+
+// Sizes (and allocates when needed) the per-warp workspace for a launch.
+int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t frame_max, int32_t max_nU,
+                     const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor)
+{
+    const int64_t ncap = std::max<int64_t>(nc_max, 32);
+    const int64_t urow = round_up(std::max<int64_t>(urow_max, 256), 256);
+    const int64_t scratch = round_up(5 * round_up(4 * ncap, 16) + 16 * ncap + urow + 256, 256);
+    int64_t stack = stack_bytes_req > 0 ? stack_bytes_req : (int64_t)stack_factor * frame_max + (1 << 20);
+    stack = round_up(stack, 256);
+    const int64_t arena = stack + scratch;
+    const int64_t slot = round_up(std::max<int64_t>(frame_max, 4096), 256);
+    const int64_t mark_stride = round_up(std::max<int32_t>(max_nU, 1), 64);
+    int n_warps = shape.warps;
+
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return MBE_ERR_CUDA;
+    const int64_t per_warp = arena + slot + 4 * mark_stride + 4;
+    // an existing workspace is reused when every region is large enough; the
+    // scratch split is recomputed for this graph inside the same arena
+    const bool fits_current = ws.arena && ws.threads == shape.threads && ws.arena_bytes >= arena &&
+                              ws.slot_bytes >= slot && ws.mark_stride >= mark_stride &&
+                              (ws.n_warps == n_warps || ws.budget_limited);
+    if (fits_current) {
+        ws.scratch_bytes = scratch;
+        ws.n_cand_cap = ncap;
+        ws.urow_bytes = urow;
+        return MBE_OK;
+    }
+    if (ws.arena) {
+        free_b += (size_t)(ws.arena_bytes + ws.slot_bytes + 4 * ws.mark_stride + 4) * ws.n_warps;
+        ws.release();
+    }
+    const int64_t budget = (int64_t)(0.75 * (double)free_b);
+    bool limited = false;
+    if (per_warp * (int64_t)n_warps > budget) {
+        limited = true;
+        // fewer resident workers rather than failing: whole blocks only
+        int warps_per_block = shape.threads / 32;
+        int blocks = (int)(budget / per_warp) / warps_per_block;
+        if (blocks < 1) return MBE_ERR_OOM;
+        n_warps = blocks * warps_per_block;
+    }
+    if (cudaMalloc(&ws.arena, (size_t)arena * n_warps) != cudaSuccess ||
+        cudaMalloc(&ws.slots, (size_t)slot * n_warps) != cudaSuccess ||
+        cudaMalloc(&ws.slot_state, sizeof(int32_t) * (size_t)n_warps) != cudaSuccess ||
+        cudaMalloc(&ws.mark, sizeof(int32_t) * (size_t)mark_stride * n_warps) != cudaSuccess ||
+        cudaMalloc(&ws.ctl, sizeof(Ctl)) != cudaSuccess) {
+        cudaGetLastError();
+        ws.release();
+        return MBE_ERR_OOM;
+    }
+    if (cudaMemset(ws.mark, 0xff, sizeof(int32_t) * (size_t)mark_stride * n_warps) != cudaSuccess) {
+        ws.release();
+        return MBE_ERR_CUDA;
+    }
+    ws.arena_bytes = arena;
+    ws.scratch_bytes = scratch;
+    ws.slot_bytes = slot;
+    ws.mark_stride = mark_stride;
+    ws.n_warps = n_warps;
+    ws.threads = shape.threads;
+    ws.blocks = n_warps / (shape.threads / 32);
+    ws.n_cand_cap = ncap;
+    ws.urow_bytes = urow;
+    ws.budget_limited = limited;
+    return MBE_OK;
+}
+
+struct RunInput {
+    const int32_t *u_off, *u_adj, *v_off, *v_adj;
+    const GraphDesc *d_desc;
+    int32_t n_graphs;
+    int32_t max_nU;
+    const int32_t *task_root, *task_graph;
+    int64_t n_tasks;
+    int64_t nc_max, urow_max, frame_max;
+    unsigned long long *per_owner; // [n_owner][4], zeroed here before every launch
+    int64_t n_owner;
+    int32_t per_mode;
+};
+
+// One persistent search launch (with automatic arena growth on overflow).
+int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStream_t s, mbe_result *out,
+               mbe_biclique_buffer *bic)
+{
+    LaunchShape shape = choose_shape(o);
+    int stack_factor = 2;
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        int st = ensure_workspace(ws, in.nc_max, in.urow_max, in.frame_max, in.max_nU, shape, o.arena_bytes,
+                                  stack_factor);
+        if (st != MBE_OK) return st;
+        if (ws.marks_dirty) {
+            MBE_TRY(cudaMemsetAsync(ws.mark, 0xff, sizeof(int32_t) * (size_t)ws.mark_stride * ws.n_warps, s));
+            ws.marks_dirty = false;
+        }
+        MBE_TRY(cudaMemsetAsync(ws.ctl, 0, sizeof(Ctl), s));
+        if (in.per_owner)
+            MBE_TRY(cudaMemsetAsync(in.per_owner, 0, sizeof(unsigned long long) * 4 * (size_t)in.n_owner, s));
+        MBE_TRY(cudaMemsetAsync(ws.slot_state, 0, sizeof(int32_t) * (size_t)ws.n_warps, s));
+        SearchArgs a;
+        memset(&a, 0, sizeof(a));
+        a.u_off = in.u_off;
+        a.u_adj = in.u_adj;
+        a.v_off = in.v_off;
+        a.v_adj = in.v_adj;
+        a.graphs = in.d_desc;
+        a.n_graphs = in.n_graphs;
+        a.key_shift = key_bits_for(std::max<int32_t>(in.max_nU, 2));
+        a.task_root = in.task_root;
+        a.task_graph = in.task_graph;
+        a.n_tasks = in.n_tasks;
+        a.arena = ws.arena;
+        a.arena_bytes = ws.arena_bytes;
+        a.scratch_bytes = ws.scratch_bytes;
+        a.stack_bytes = ws.arena_bytes - ws.scratch_bytes;
+        if (o.arena_bytes > 0) a.stack_bytes = std::min<int64_t>(a.stack_bytes, round_up(o.arena_bytes, 256));
+        a.slots = ws.slots;
+        a.slot_bytes = ws.slot_bytes;
+        a.slot_state = ws.slot_state;
+        a.mark = ws.mark;
+        a.mark_stride = ws.mark_stride;
+        a.n_cand_cap = ws.n_cand_cap;
+        a.urow_bytes = ws.urow_bytes;
+        a.cursor = &ws.ctl->cursor;
+        a.n_idle = &ws.ctl->n_idle;
+        a.outstanding = &ws.ctl->outstanding;
+        a.error = &ws.ctl->error;
+        a.watchdog_ns = (long long)(o.watchdog_ms > 0 ? o.watchdog_ms : 60000) * 1000000LL;
+        a.deadline_ns = deadline_ms() * 1000000LL;
+        a.n_published = &ws.ctl->n_published;
+        a.debug = debug_buffer(ws.n_warps);
+        a.steal = o.steal ? 1 : 0;
+        a.n_warps = ws.n_warps;
+        a.max_words = o.bitset_max_words > 0 ? std::min(o.bitset_max_words, 32) : 32;
+        a.totals = ws.ctl->totals;
+        a.per_task_owner = in.per_owner;
+        a.per_root_mode = in.per_mode;
+        a.emit = (o.emit && bic) ? 1 : 0;
+        if (a.emit) {
+            a.out_ids = bic->ids;
+            a.cap_ids = bic->capacity_ids;
+            a.out_offsets = bic->offsets;
+            a.cap_bic = bic->capacity_bicliques;
+            a.used_ids = &ws.ctl->used_ids;
+            a.used_bic = &ws.ctl->used_bic;
+        }
+        cudaEvent_t e0, e1;
+        MBE_TRY(cudaEventCreate(&e0));
+        MBE_TRY(cudaEventCreate(&e1));
+        cudaEventRecord(e0, s);
+        cudaError_t le = launch_search(a, ws.blocks, ws.threads, s);
+        cudaEventRecord(e1, s);
+        Ctl h;
+        cudaError_t ce = cudaMemcpyAsync(&h, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+        cudaError_t se = cudaStreamSynchronize(s);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (le != cudaSuccess) return cuda_status(le);
+        if (ce != cudaSuccess) return cuda_status(ce);
+        if (se != cudaSuccess) return cuda_status(se);
+        if (h.error != 0) ws.marks_dirty = true;
+        if (h.error == MBE_ERR_ARENA_FULL && o.arena_bytes == 0) {
+            stack_factor *= 4; // grow the stacks and run again from scratch
+            continue;
+        }
+        if (out) {
+            out->count = h.totals[0];
+            out->hash = h.totals[1];
+            out->nodes = h.totals[2];
+            out->bytes_alg = h.totals[3];
+            out->n_donations = h.totals[4];
+            out->device_ms = ms;
+            out->n_workers = ws.n_warps;
+        }
+        if (a.emit) {
+            bic->n_ids_written = (int64_t)h.used_ids;
+            bic->n_bicliques_written = (int64_t)h.used_bic;
+        }
+        return h.error;
+    }
+    return MBE_ERR_ARENA_FULL;
+}
+
+} // namespace
+} // namespace mbe
+
+using namespace mbe;
+
+extern "C" {
+
+const char *mbe_status_string(int status)
+{
+    switch (status) {
+    case MBE_OK: return "MBE_OK";
+    case MBE_ERR_INVALID_ARG: return "MBE_ERR_INVALID_ARG";
+    case MBE_ERR_INVALID_GRAPH: return "MBE_ERR_INVALID_GRAPH";
+    case MBE_ERR_OOM: return "MBE_ERR_OOM";
+    case MBE_ERR_ARENA_FULL: return "MBE_ERR_ARENA_FULL";
+    case MBE_ERR_OUTPUT_FULL: return "MBE_ERR_OUTPUT_FULL";
+    case MBE_ERR_TIMEOUT: return "MBE_ERR_TIMEOUT";
+    case MBE_ERR_CUDA: return "MBE_ERR_CUDA";
+    case MBE_ERR_UNSUPPORTED: return "MBE_ERR_UNSUPPORTED";
+    default: return "MBE_ERR_UNKNOWN";
+    }
+}
+
+int mbe_default_options(mbe_options *opt)
+{
+    if (!opt) return MBE_ERR_INVALID_ARG;
+    memset(opt, 0, sizeof(*opt));
+    opt->steal = 1;
+    opt->root_end = -1;
+    return MBE_OK;
+}
+
+int mbe_graph_destroy(mbe_graph *g)
+{
+    if (!g) return MBE_OK;
+    cudaFree(g->u_off);
+    cudaFree(g->u_adj);
+    cudaFree(g->v_off);
+    cudaFree(g->v_adj);
+    cudaFree(g->d_desc);
+    cudaFree(g->order_static);
+    cudaFree(g->hist);
+    delete g;
+    return MBE_OK;
+}
+
+int mbe_graph_create(int32_t nU, int32_t nV, int64_t nE, const int32_t *u_off, const int32_t *u_adj,
+                     const int32_t *v_off, const int32_t *v_adj, int32_t ptr_kind, void *stream, mbe_graph **out)
+{
+    if (!out) return MBE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (nU < 0 || nV < 0 || nE < 0 || nE >= ((int64_t)1 << 31) || (ptr_kind != 0 && ptr_kind != 1))
+        return MBE_ERR_INVALID_ARG;
+    if (!u_off || !v_off || (nE > 0 && (!u_adj || !v_adj))) return MBE_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    mbe_graph *g = new mbe_graph();
+    g->nU = nU;
+    g->nV = nV;
+    g->nE = nE;
+    cudaGetDevice(&g->device);
+    auto fail = [&](int st) {
+        mbe_graph_destroy(g);
+        return st;
+    };
+    const size_t eb = sizeof(int32_t) * (size_t)std::max<int64_t>(nE, 1);
+    if (cudaMalloc(&g->u_off, sizeof(int32_t) * (size_t)(nU + 1)) != cudaSuccess ||
+        cudaMalloc(&g->v_off, sizeof(int32_t) * (size_t)(nV + 1)) != cudaSuccess ||
+        cudaMalloc(&g->u_adj, eb) != cudaSuccess || cudaMalloc(&g->v_adj, eb) != cudaSuccess ||
+        cudaMalloc(&g->d_desc, sizeof(GraphDesc)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MBE_ERR_OOM);
+    }
+    cudaMemcpyKind kind = ptr_kind == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    if (cudaMemcpyAsync(g->u_off, u_off, sizeof(int32_t) * (size_t)(nU + 1), kind, s) != cudaSuccess ||
+        cudaMemcpyAsync(g->v_off, v_off, sizeof(int32_t) * (size_t)(nV + 1), kind, s) != cudaSuccess ||
+        (nE > 0 && cudaMemcpyAsync(g->u_adj, u_adj, sizeof(int32_t) * (size_t)nE, kind, s) != cudaSuccess) ||
+        (nE > 0 && cudaMemcpyAsync(g->v_adj, v_adj, sizeof(int32_t) * (size_t)nE, kind, s) != cudaSuccess)) {
+        cudaGetLastError();
+        return fail(MBE_ERR_CUDA);
+    }
+    GraphDesc desc{0, 0, 0, nU, nV};
+    unsigned long long *d_bounds = nullptr;
+    int32_t *d_bad = nullptr;
+    if (cudaMalloc(&d_bounds, sizeof(unsigned long long) * 8) != cudaSuccess ||
+        cudaMalloc(&d_bad, sizeof(int32_t)) != cudaSuccess) {
+        cudaFree(d_bounds);
+        cudaGetLastError();
+        return fail(MBE_ERR_OOM);
+    }
+    unsigned long long hb[8] = {0};
+    int32_t hbad = 0;
+    cudaError_t e = cudaMemcpyAsync(g->d_desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bounds, 0, sizeof(unsigned long long) * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = validate_graph(g->u_off, g->u_adj, g->v_off, g->v_adj, nU, nV, nE, d_bad, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && hbad == 0 && nU > 0)
+        e = root_bounds(g->d_desc, 1, nU, g->u_off, g->u_adj, g->v_off, d_bounds, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d_bounds, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_bounds);
+    cudaFree(d_bad);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(cuda_status(e));
+    }
+    if (hbad != 0) return fail(MBE_ERR_INVALID_GRAPH);
+    g->nc_max = (int64_t)hb[0];
+    g->urow_max = (int64_t)hb[1];
+    g->frame_max = (int64_t)hb[2];
+    g->max_deg_u = (int32_t)hb[3];
+    g->n_live = (int32_t)hb[4];
+    {
+        int32_t *d_m = nullptr, hm = 0;
+        e = cudaMalloc(&d_m, sizeof(int32_t));
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_m, 0, sizeof(int32_t), s);
+        if (e == cudaSuccess && nV > 0) e = max_degree(g->v_off, nV, d_m, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hm, d_m, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(d_m);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(cuda_status(e));
+        }
+        g->max_deg_v = hm;
+    }
+    g->hist_len = std::max<int32_t>(g->max_deg_u, 4096) + 1;
+    if (cudaMalloc(&g->order_static, sizeof(int32_t) * (size_t)std::max(nU, 1)) != cudaSuccess ||
+        cudaMalloc(&g->hist, sizeof(int32_t) * (size_t)g->hist_len) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MBE_ERR_OOM);
+    }
+    if (nU > 0) {
+        e = order_by_degree_desc(g->u_off, nU, g->max_deg_u, g->hist, g->order_static, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(cuda_status(e));
+        }
+    }
+    *out = g;
+    return MBE_OK;
+}
+
+// Copies the progress records of the last launch (8 u64 per worker) to host
+// memory; returns the number of workers recorded (0 unless MBE_DEBUG_TRACE).
+int mbe_debug_trace(uint64_t *host, int32_t max_workers)
+{
+    if (!g_debug || !host) return 0;
+    int n = std::min(max_workers, g_debug_warps);
+    if (cudaMemcpy(host, g_debug, sizeof(uint64_t) * 16 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    return n;
+}
+
+int mbe_release_workspace(void)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < kMaxDevices) g_ws[dev].release();
+    return MBE_OK;
+}
+
+int mbe_graph_info(const mbe_graph *g, int32_t *nU, int32_t *nV, int64_t *nE, int32_t *max_deg_u,
+                   int32_t *max_deg_v)
+{
+    if (!g) return MBE_ERR_INVALID_ARG;
+    if (nU) *nU = g->nU;
+    if (nV) *nV = g->nV;
+    if (nE) *nE = g->nE;
+    if (max_deg_u) *max_deg_u = g->max_deg_u;
+    if (max_deg_v) *max_deg_v = g->max_deg_v;
+    return MBE_OK;
+}
+
+int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mbe_result *out,
+                  mbe_biclique_buffer *bicliques)
+{
+    if (out) memset(out, 0, sizeof(*out));
+    if (!gc) return set_status(out, MBE_ERR_INVALID_ARG);
+    mbe_graph *g = const_cast<mbe_graph *>(gc);
+    mbe_options o;
+    mbe_default_options(&o);
+    if (opts) o = *opts;
+    if (o.emit && !bicliques) return set_status(out, MBE_ERR_INVALID_ARG);
+    if (o.emit && (!bicliques->ids || !bicliques->offsets || bicliques->capacity_ids < 0 ||
+                   bicliques->capacity_bicliques < 0))
+        return set_status(out, MBE_ERR_INVALID_ARG);
+    if (o.block_threads < 0 || o.blocks_per_sm < 0 || o.watchdog_ms < 0 || o.arena_bytes < 0)
+        return set_status(out, MBE_ERR_INVALID_ARG);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->nU == 0 || g->n_live == 0) return set_status(out, MBE_OK);
+
+    const int32_t *order = g->order_static;
+    int64_t n_order = g->n_live;
+    if (o.exec_order) {
+        if (o.n_exec < 0 || o.n_exec > g->nU) return set_status(out, MBE_ERR_INVALID_ARG);
+        order = o.exec_order;
+        n_order = o.n_exec;
+    } else if (o.schedule == 1) {
+        return set_status(out, MBE_ERR_UNSUPPORTED);
+    }
+    int64_t b = std::max<int64_t>(0, o.root_begin);
+    int64_t e = o.root_end < 0 ? n_order : std::min<int64_t>(o.root_end, n_order);
+    if (b > e) return set_status(out, MBE_ERR_INVALID_ARG);
+
+    RunInput in;
+    in.u_off = g->u_off;
+    in.u_adj = g->u_adj;
+    in.v_off = g->v_off;
+    in.v_adj = g->v_adj;
+    in.d_desc = g->d_desc;
+    in.n_graphs = 1;
+    in.max_nU = g->nU;
+    in.task_root = order + b;
+    in.task_graph = nullptr;
+    in.n_tasks = e - b;
+    in.nc_max = g->nc_max;
+    in.urow_max = g->urow_max;
+    in.frame_max = g->frame_max;
+    in.per_owner = reinterpret_cast<unsigned long long *>(o.per_root);
+    in.n_owner = g->nU;
+    in.per_mode = 1;
+    int st = run_search(device_workspace(), in, o, s, out, bicliques);
+    return set_status(out, st);
+}
+
+int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t *nU, const int32_t *nV,
+                        const int64_t *u_off_start, const int64_t *v_off_start, const int32_t *u_off_cat,
+                        const int32_t *u_adj_cat, const int32_t *v_off_cat, const int32_t *v_adj_cat,
+                        const mbe_options *opts, void *stream, mbe_result *per_graph, mbe_result *total)
+{
+    if (total) memset(total, 0, sizeof(*total));
+    if (n_graphs < 0 || (n_graphs > 0 && (!edge_off || !nU || !nV || !u_off_start || !v_off_start || !u_off_cat ||
+                                          !v_off_cat || !per_graph)))
+        return set_status(total, MBE_ERR_INVALID_ARG);
+    if (n_graphs == 0) return set_status(total, MBE_OK);
+    mbe_options o;
+    mbe_default_options(&o);
+    if (opts) o = *opts;
+    o.emit = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // host-side descriptors and the task list (graphs by falling density x size, roots by falling degree)
+    std::vector<GraphDesc> desc((size_t)n_graphs);
+    int64_t n_uoff = 0, n_voff = 0, nE = edge_off[n_graphs];
+    int32_t max_nU = 1;
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        if (nU[i] < 0 || nV[i] < 0 || nU[i] > 65536 || edge_off[i + 1] < edge_off[i])
+            return set_status(total, MBE_ERR_INVALID_ARG);
+        desc[i] = GraphDesc{u_off_start[i], v_off_start[i], edge_off[i], nU[i], nV[i]};
+        n_uoff = std::max<int64_t>(n_uoff, u_off_start[i] + nU[i] + 1);
+        n_voff = std::max<int64_t>(n_voff, v_off_start[i] + nV[i] + 1);
+        max_nU = std::max(max_nU, nU[i]);
+    }
+    if (nE > 0 && (!u_adj_cat || !v_adj_cat)) return set_status(total, MBE_ERR_INVALID_ARG);
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        const int32_t *uo = u_off_cat + u_off_start[i];
+        const int32_t *vo = v_off_cat + v_off_start[i];
+        if (uo[0] != 0 || vo[0] != 0 || (int64_t)uo[nU[i]] != edge_off[i + 1] - edge_off[i] ||
+            (int64_t)vo[nV[i]] != edge_off[i + 1] - edge_off[i])
+            return set_status(total, MBE_ERR_INVALID_GRAPH);
+        for (int32_t u = 0; u < nU[i]; ++u)
+            if ((uo[u + 1] - uo[u]) > 64 * 32) return set_status(total, MBE_ERR_UNSUPPORTED);
+    }
+    std::vector<int32_t> gorder((size_t)n_graphs);
+    for (int32_t i = 0; i < n_graphs; ++i) gorder[i] = i;
+    std::vector<double> gkey((size_t)n_graphs);
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        double ne = (double)(edge_off[i + 1] - edge_off[i]);
+        double dens = (nU[i] && nV[i]) ? ne / ((double)nU[i] * nV[i]) : 0.0;
+        gkey[i] = ne * dens * dens;
+    }
+    std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) { return gkey[a] > gkey[b]; });
+    std::vector<int32_t> troot, tgraph;
+    troot.reserve((size_t)n_uoff);
+    tgraph.reserve((size_t)n_uoff);
+    std::vector<std::pair<int32_t, int32_t>> tmp;
+    for (int32_t gi : gorder) {
+        const int32_t *uo = u_off_cat + u_off_start[gi];
+        tmp.clear();
+        for (int32_t u = 0; u < nU[gi]; ++u) {
+            int32_t d = uo[u + 1] - uo[u];
+            if (d > 0) tmp.push_back({-d, u});
+        }
+        std::sort(tmp.begin(), tmp.end());
+        for (auto &p : tmp) {
+            troot.push_back(p.second);
+            tgraph.push_back(gi);
+        }
+    }
+    const int64_t n_tasks = (int64_t)troot.size();
+
+    int32_t *d_uo = nullptr, *d_vo = nullptr, *d_ua = nullptr, *d_va = nullptr, *d_tr = nullptr, *d_tg = nullptr,
+            *d_bad = nullptr;
+    GraphDesc *d_desc = nullptr;
+    unsigned long long *d_bounds = nullptr, *d_owner = nullptr;
+    Workspace &ws = device_workspace();
+    int st = MBE_OK;
+    auto cleanup = [&]() {
+        cudaFree(d_uo);
+        cudaFree(d_vo);
+        cudaFree(d_ua);
+        cudaFree(d_va);
+        cudaFree(d_tr);
+        cudaFree(d_tg);
+        cudaFree(d_bad);
+        cudaFree(d_desc);
+        cudaFree(d_bounds);
+        cudaFree(d_owner);
+    };
+    const size_t eb = sizeof(int32_t) * (size_t)std::max<int64_t>(nE, 1);
+    if (cudaMalloc(&d_uo, sizeof(int32_t) * (size_t)n_uoff) != cudaSuccess ||
+        cudaMalloc(&d_vo, sizeof(int32_t) * (size_t)n_voff) != cudaSuccess || cudaMalloc(&d_ua, eb) != cudaSuccess ||
+        cudaMalloc(&d_va, eb) != cudaSuccess ||
+        cudaMalloc(&d_tr, sizeof(int32_t) * (size_t)std::max<int64_t>(n_tasks, 1)) != cudaSuccess ||
+        cudaMalloc(&d_tg, sizeof(int32_t) * (size_t)std::max<int64_t>(n_tasks, 1)) != cudaSuccess ||
+        cudaMalloc(&d_bad, sizeof(int32_t)) != cudaSuccess ||
+        cudaMalloc(&d_desc, sizeof(GraphDesc) * (size_t)n_graphs) != cudaSuccess ||
+        cudaMalloc(&d_bounds, sizeof(unsigned long long) * 8) != cudaSuccess ||
+        cudaMalloc(&d_owner, sizeof(unsigned long long) * 4 * (size_t)n_graphs) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return set_status(total, MBE_ERR_OOM);
+    }
+    cudaError_t e = cudaMemcpyAsync(d_uo, u_off_cat, sizeof(int32_t) * (size_t)n_uoff, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_vo, v_off_cat, sizeof(int32_t) * (size_t)n_voff, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nE > 0) e = cudaMemcpyAsync(d_ua, u_adj_cat, eb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && nE > 0) e = cudaMemcpyAsync(d_va, v_adj_cat, eb, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_tasks > 0)
+        e = cudaMemcpyAsync(d_tr, troot.data(), sizeof(int32_t) * (size_t)n_tasks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n_tasks > 0)
+        e = cudaMemcpyAsync(d_tg, tgraph.data(), sizeof(int32_t) * (size_t)n_tasks, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_desc, desc.data(), sizeof(GraphDesc) * (size_t)n_graphs, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_bounds, 0, sizeof(unsigned long long) * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_owner, 0, sizeof(unsigned long long) * 4 * (size_t)n_graphs, s);
+    for (int32_t i = 0; i < n_graphs && e == cudaSuccess; ++i)
+        e = validate_graph(d_uo + u_off_start[i], d_ua + edge_off[i], d_vo + v_off_start[i], d_va + edge_off[i],
+                           nU[i], nV[i], edge_off[i + 1] - edge_off[i], d_bad, s);
+    if (e == cudaSuccess) e = root_bounds(d_desc, n_graphs, max_nU, d_uo, d_ua, d_vo, d_bounds, s);
+    unsigned long long hb[8] = {0};
+    int32_t hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d_bounds, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return set_status(total, cuda_status(e));
+    }
+    if (hbad) {
+        cleanup();
+        return set_status(total, MBE_ERR_INVALID_GRAPH);
+    }
+    RunInput in;
+    in.u_off = d_uo;
+    in.u_adj = d_ua;
+    in.v_off = d_vo;
+    in.v_adj = d_va;
+    in.d_desc = d_desc;
+    in.n_graphs = n_graphs;
+    in.max_nU = max_nU;
+    in.task_root = d_tr;
+    in.task_graph = d_tg;
+    in.n_tasks = n_tasks;
+    in.nc_max = (int64_t)hb[0];
+    in.urow_max = (int64_t)hb[1];
+    in.frame_max = (int64_t)hb[2];
+    in.per_owner = d_owner;
+    in.n_owner = n_graphs;
+    in.per_mode = 2;
+    st = n_tasks > 0 ? run_search(ws, in, o, s, total, nullptr) : MBE_OK;
+    std::vector<unsigned long long> res((size_t)n_graphs * 4);
+    if (st == MBE_OK || st == MBE_ERR_TIMEOUT) {
+        e = cudaMemcpy(res.data(), d_owner, sizeof(unsigned long long) * 4 * (size_t)n_graphs, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_status(e);
+    }
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        mbe_result &r = per_graph[i];
+        memset(&r, 0, sizeof(r));
+        r.count = res[4 * i + 0];
+        r.hash = res[4 * i + 1];
+        r.nodes = res[4 * i + 2];
+        r.bytes_alg = res[4 * i + 3];
+        r.status = st;
+    }
+    cleanup();
+    return set_status(total, st);
+}
+
+} // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mbe.h"
+
+namespace mbe {
+
+// One graph of a launch. For a single graph there is one descriptor with
+// zero bases; for a batch, graph g's arrays start at these bases of the
+// concatenated arrays.
+struct GraphDesc {
+    int64_t u_off_base;  // index of the graph's u_off[0] in the concatenated u_off
+    int64_t v_off_base;  // index of its v_off[0]
+    int64_t edge_base;   // index of its first edge in u_adj / v_adj
+    int32_t nU, nV;
+};
+
+// Everything the persistent search kernel reads. All pointers are device pointers.
+struct SearchArgs {
+    const int32_t *u_off, *u_adj, *v_off, *v_adj; // concatenated for a batch
+    const GraphDesc *graphs;
+    int32_t n_graphs;
+    int32_t key_shift;      // bits for a vertex id in the (count, id) sort key
+    const int32_t *task_root;  // [n_tasks] root (graph-local id) in execution order
+    const int32_t *task_graph; // [n_tasks] graph of the task, NULL when n_graphs == 1
+    int64_t n_tasks;
+
+    // per-worker workspace
+    char *arena;          // n_warps * arena_bytes
+    int64_t arena_bytes;  // per warp: [stack ... | scratch]
+    int64_t scratch_bytes;
+    int64_t stack_bytes;  // usable stack (<= arena_bytes - scratch_bytes)
+    char *slots;          // n_warps * slot_bytes, donation slots
+    int64_t slot_bytes;
+    int32_t *slot_state;  // [n_warps]
+    int32_t *mark;        // n_warps * mark_stride, all -1 between uses
+    int64_t mark_stride;
+    int64_t n_cand_cap;   // largest candidate count of any root (bounds every frame)
+    int64_t urow_bytes;   // largest root-universe row storage
+
+    // control
+    unsigned long long *cursor;   // next task
+    int32_t *n_idle;              // workers looking for work
+    long long *outstanding;       // tasks claimed or published and not finished
+    int32_t *error;               // first error status, 0 = none
+    long long watchdog_ns;        // longest idle wait of a worker
+    long long deadline_ns;        // longest run of the whole launch, measured by every worker
+    int32_t *n_published;         // donation slots currently FULL
+    unsigned long long *debug;    // optional [n_warps][8] progress records
+    int32_t steal;
+    int32_t n_warps;
+    int32_t max_words;
+
+    // outputs
+    unsigned long long *totals;   // [8]: count, hash, nodes, bytes, donations, steals, -, -
+    unsigned long long *per_task_owner; // [n_owner][4] per root (single) or per graph (batch), or NULL
+    int32_t per_root_mode;        // 1: index per_task_owner by root id, 2: by graph id
+
+    // biclique output (emit)
+    int32_t emit;
+    int32_t *out_ids;
+    int64_t cap_ids;
+    int64_t *out_offsets;
+    int64_t cap_bic;
+    unsigned long long *used_ids;
+    unsigned long long *used_bic;
+};
+
+// Status codes the kernel writes into *error.
+enum : int32_t {
+    kErrArena = MBE_ERR_ARENA_FULL,
+    kErrTimeout = MBE_ERR_TIMEOUT,
+    kErrUnsupported = MBE_ERR_UNSUPPORTED,
+};
+
+// Launch the persistent search kernel on stream (grid = blocks, block = threads).
+cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
+
+// Bytes of per-warp shared memory the search kernel uses.
+int search_smem_per_warp();
+
+// Resident blocks per SM for a block of `threads` threads, at most
+// blocks_per_sm_req; a negative value -t means `threads` exceeds the
+// kernel's limit and t is the largest allowed block size.
+int search_fit_shape(int threads, int blocks_per_sm_req);
+
+} // namespace mbe

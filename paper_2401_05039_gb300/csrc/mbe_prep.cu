@@ -1,0 +1,227 @@
+// Preprocessing kernels: input validation, per-root workspace bounds and the
+// static execution order of the roots.
+#include "mbe_internal.h"
+#include "mbe_prep.h"
+
+namespace mbe {
+namespace {
+
+// CSR well-formedness: offsets start at 0, end at nE and never decrease;
+// every list strictly increasing (sorted, no duplicates) with ids in
+// [0, n_other). One thread per vertex.
+__global__ void validate_csr_kernel(const int32_t *off, const int32_t *adj, int32_t n, int32_t n_other, int64_t nE,
+                                    int32_t *bad)
+{
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += stride) {
+        if (i == 0 && off[0] != 0) atomicOr(bad, 1);
+        if (i == n) {
+            if ((int64_t)off[n] != nE) atomicOr(bad, 2);
+            continue;
+        }
+        int a = off[i], b = off[i + 1];
+        if (b < a || a < 0 || (int64_t)b > nE) {
+            atomicOr(bad, 4);
+            continue;
+        }
+        int prev = -1;
+        for (int k = a; k < b; ++k) {
+            int x = adj[k];
+            if (x <= prev || x >= n_other) {
+                atomicOr(bad, 8);
+                break;
+            }
+            prev = x;
+        }
+    }
+}
+
+// Every (u, v) of the U-side CSR appears in N(v) of the V-side CSR. With
+// both forms duplicate-free and of equal size, this makes them transposes.
+__global__ void validate_transpose_kernel(const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
+                                          const int32_t *v_adj, int32_t nU, int32_t *bad)
+{
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nU; u += stride) {
+        for (int k = u_off[u]; k < u_off[u + 1]; ++k) {
+            int v = u_adj[k];
+            int lo = v_off[v], hi = v_off[v + 1];
+            while (lo < hi) {
+                int mid = lo + ((hi - lo) >> 1);
+                if (v_adj[mid] < u) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= v_off[v + 1] || v_adj[lo] != (int32_t)u) {
+                atomicOr(bad, 16);
+                break;
+            }
+        }
+    }
+}
+
+// Per-root bounds of the search workspace. For root r with d = |N(r)|, its
+// local universe has at most nc = min(sum_{w in N(r)} (|N(w)| - 1), nU - 1)
+// candidates, rows of W = ceil(d/64) words, and the level-1 frame holds at
+// most nc rows. out: [0] max nc, [1] max universe row bytes, [2] max level-1
+// frame bytes, [3] max degree, [4] number of non-isolated roots.
+__global__ void root_bounds_kernel(const GraphDesc *graphs, int32_t n_graphs, const int32_t *u_off_cat,
+                                   const int32_t *u_adj_cat, const int32_t *v_off_cat, unsigned long long *out)
+{
+    int g = blockIdx.y;
+    if (g >= n_graphs) return;
+    GraphDesc G = graphs[g];
+    const int32_t *u_off = u_off_cat + G.u_off_base;
+    const int32_t *v_off = v_off_cat + G.v_off_base;
+    const int32_t *u_adj = u_adj_cat + G.edge_base;
+    unsigned long long m_nc = 0, m_urow = 0, m_frame = 0, m_deg = 0, live = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < G.nU; r += gridDim.x * blockDim.x) {
+        int a = u_off[r], d = u_off[r + 1] - a;
+        if (d == 0) continue;
+        long long s = 0;
+        for (int k = 0; k < d; ++k) {
+            int w = u_adj[a + k];
+            s += v_off[w + 1] - v_off[w] - 1;
+        }
+        long long nc = s < (long long)G.nU - 1 ? s : (long long)G.nU - 1;
+        long long W = (d + 63) / 64;
+        long long tiles = (nc + 31) / 32;
+        unsigned long long urow = 256ULL * W * tiles;
+        unsigned long long frame = 64 + ((4ULL * d + 15) & ~15ULL) + 2 * ((4ULL * nc + 15) & ~15ULL) + urow + 16;
+        m_nc = max(m_nc, (unsigned long long)nc);
+        m_urow = max(m_urow, urow);
+        m_frame = max(m_frame, frame);
+        m_deg = max(m_deg, (unsigned long long)d);
+        live += 1;
+    }
+    atomicMax(out + 0, m_nc);
+    atomicMax(out + 1, m_urow);
+    atomicMax(out + 2, m_frame);
+    atomicMax(out + 3, m_deg);
+    atomicAdd(out + 4, live);
+}
+
+__global__ void degree_hist_kernel(const int32_t *u_off, int32_t nU, int32_t *hist)
+{
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nU; u += gridDim.x * blockDim.x) {
+        int d = u_off[u + 1] - u_off[u];
+        if (d > 0) atomicAdd(hist + d, 1);
+    }
+}
+
+// Exclusive scan of hist[0..n) from the top bin down (descending keys first),
+// one block, in place: hist[b] = number of items with key > b.
+__global__ void scan_desc_kernel(int32_t *hist, int32_t n)
+{
+    __shared__ int32_t carry;
+    __shared__ int32_t part[1024];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = n - 1; base >= 0; base -= blockDim.x) {
+        int b = base - (int)threadIdx.x;
+        int v = b >= 0 ? hist[b] : 0;
+        part[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+            int y = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+            __syncthreads();
+            part[threadIdx.x] += y;
+            __syncthreads();
+        }
+        int excl = part[threadIdx.x] - v + carry;
+        if (b >= 0) hist[b] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry += part[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+__global__ void scatter_by_degree_kernel(const int32_t *u_off, int32_t nU, int32_t *pos, int32_t *order)
+{
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < nU; u += gridDim.x * blockDim.x) {
+        int d = u_off[u + 1] - u_off[u];
+        if (d > 0) order[atomicAdd(pos + d, 1)] = u;
+    }
+}
+
+// Roots ordered by a non-negative integer key, descending (ties in any order).
+__global__ void key_hist_kernel(const int32_t *key, int32_t n, int32_t *hist)
+{
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+        if (key[u] >= 0) atomicAdd(hist + key[u], 1);
+}
+
+__global__ void key_scatter_kernel(const int32_t *key, int32_t n, int32_t *pos, int32_t *order)
+{
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < n; u += gridDim.x * blockDim.x)
+        if (key[u] >= 0) order[atomicAdd(pos + key[u], 1)] = u;
+}
+
+__global__ void max_degree_kernel(const int32_t *off, int32_t n, int32_t *out)
+{
+    int m = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = max(m, off[i + 1] - off[i]);
+    atomicMax(out, m);
+}
+
+} // namespace
+
+cudaError_t max_degree(const int32_t *off, int32_t n, int32_t *d_out, cudaStream_t s)
+{
+    int blocks = (n + 255) / 256;
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    if (blocks < 1) blocks = 1;
+    max_degree_kernel<<<blocks, 256, 0, s>>>(off, n, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t validate_graph(const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off, const int32_t *v_adj,
+                           int32_t nU, int32_t nV, int64_t nE, int32_t *d_bad, cudaStream_t s)
+{
+    int blocks = 2 * 152, threads = 256;
+    validate_csr_kernel<<<blocks, threads, 0, s>>>(u_off, u_adj, nU, nV, nE, d_bad);
+    validate_csr_kernel<<<blocks, threads, 0, s>>>(v_off, v_adj, nV, nU, nE, d_bad);
+    validate_transpose_kernel<<<blocks, threads, 0, s>>>(u_off, u_adj, v_off, v_adj, nU, d_bad);
+    return cudaGetLastError();
+}
+
+cudaError_t root_bounds(const GraphDesc *d_graphs, int32_t n_graphs, int32_t max_nU, const int32_t *u_off,
+                        const int32_t *u_adj, const int32_t *v_off, unsigned long long *d_out, cudaStream_t s)
+{
+    int gx = (max_nU + 255) / 256;
+    if (gx > 64) gx = 64;
+    if (gx < 1) gx = 1;
+    dim3 grid(gx, n_graphs);
+    root_bounds_kernel<<<grid, 256, 0, s>>>(d_graphs, n_graphs, u_off, u_adj, v_off, d_out);
+    return cudaGetLastError();
+}
+
+cudaError_t order_by_degree_desc(const int32_t *u_off, int32_t nU, int32_t max_deg, int32_t *d_hist,
+                                 int32_t *d_order, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, sizeof(int32_t) * (size_t)(max_deg + 1), s);
+    if (e != cudaSuccess) return e;
+    int blocks = (nU + 255) / 256;
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    if (blocks < 1) blocks = 1;
+    degree_hist_kernel<<<blocks, 256, 0, s>>>(u_off, nU, d_hist);
+    scan_desc_kernel<<<1, 1024, 0, s>>>(d_hist, max_deg + 1);
+    scatter_by_degree_kernel<<<blocks, 256, 0, s>>>(u_off, nU, d_hist, d_order);
+    return cudaGetLastError();
+}
+
+cudaError_t order_by_key_desc(const int32_t *d_key, int32_t n, int32_t max_key, int32_t *d_hist, int32_t *d_order,
+                              cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, sizeof(int32_t) * (size_t)(max_key + 1), s);
+    if (e != cudaSuccess) return e;
+    int blocks = (n + 255) / 256;
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    if (blocks < 1) blocks = 1;
+    key_hist_kernel<<<blocks, 256, 0, s>>>(d_key, n, d_hist);
+    scan_desc_kernel<<<1, 1024, 0, s>>>(d_hist, max_key + 1);
+    key_scatter_kernel<<<blocks, 256, 0, s>>>(d_key, n, d_hist, d_order);
+    return cudaGetLastError();
+}
+
+} // namespace mbe

@@ -1,0 +1,30 @@
+// Host launchers of the preprocessing kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mbe_internal.h"
+
+namespace mbe {
+
+// ORs a nonzero code into *d_bad when the CSR/CSC pair is malformed.
+cudaError_t validate_graph(const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off, const int32_t *v_adj,
+                           int32_t nU, int32_t nV, int64_t nE, int32_t *d_bad, cudaStream_t s);
+
+// *d_out = max(*d_out, largest list length of the CSR off[0..n]).
+cudaError_t max_degree(const int32_t *off, int32_t n, int32_t *d_out, cudaStream_t s);
+
+// Workspace bounds over all roots of all graphs; d_out[5] must be zeroed.
+cudaError_t root_bounds(const GraphDesc *d_graphs, int32_t n_graphs, int32_t max_nU, const int32_t *u_off,
+                        const int32_t *u_adj, const int32_t *v_off, unsigned long long *d_out, cudaStream_t s);
+
+// d_order receives the non-isolated U vertices by descending degree.
+// d_hist needs max_deg + 1 entries.
+cudaError_t order_by_degree_desc(const int32_t *u_off, int32_t nU, int32_t max_deg, int32_t *d_hist,
+                                 int32_t *d_order, cudaStream_t s);
+
+// d_order receives every u with d_key[u] >= 0, by descending key (keys <= max_key).
+cudaError_t order_by_key_desc(const int32_t *d_key, int32_t n, int32_t max_key, int32_t *d_hist, int32_t *d_order,
+                              cudaStream_t s);
+
+} // namespace mbe

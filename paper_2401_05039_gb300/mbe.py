@@ -1,0 +1,239 @@
+"""Thin ctypes binding of the C ABI in include/mbe.h (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/libmbe.so``; this module
+converts numpy arrays (host memory) and torch CUDA tensors (device memory)
+to raw pointers and turns status codes into exceptions. There is no CPU
+fallback: without the library (or a GPU) the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+MBE_OK = 0
+STATUS = {0: "MBE_OK", 1: "MBE_ERR_INVALID_ARG", 2: "MBE_ERR_INVALID_GRAPH", 3: "MBE_ERR_OOM",
+          4: "MBE_ERR_ARENA_FULL", 5: "MBE_ERR_OUTPUT_FULL", 6: "MBE_ERR_TIMEOUT", 7: "MBE_ERR_CUDA",
+          8: "MBE_ERR_UNSUPPORTED"}
+
+
+class MBEError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("bitset_max_words", ctypes.c_int32), ("steal", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("emit", ctypes.c_int32), ("watchdog_ms", ctypes.c_int32), ("root_begin", ctypes.c_int32),
+                ("root_end", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("model", ctypes.c_void_p),
+                ("per_root", ctypes.c_void_p), ("exec_order", ctypes.c_void_p), ("n_exec", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("hash", ctypes.c_uint64), ("nodes", ctypes.c_uint64),
+                ("bytes_alg", ctypes.c_uint64), ("device_ms", ctypes.c_double), ("prep_ms", ctypes.c_double),
+                ("status", ctypes.c_int32), ("n_workers", ctypes.c_int32), ("n_donations", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class BicliqueBuffer(ctypes.Structure):
+    _fields_ = [("ids", ctypes.c_void_p), ("capacity_ids", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("capacity_bicliques", ctypes.c_int64), ("n_ids_written", ctypes.c_int64),
+                ("n_bicliques_written", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+
+_SIGNATURES = {
+    "mbe_status_string": ([_I32], ctypes.c_char_p),
+    "mbe_graph_create": ([_I32, _I32, _I64, _P, _P, _P, _P, _I32, _P, ctypes.POINTER(_P)], _I32),
+    "mbe_graph_destroy": ([_P], _I32),
+    "mbe_graph_info": ([_P, _P, _P, _P, _P, _P], _I32),
+    "mbe_default_options": ([ctypes.POINTER(Options)], _I32),
+    "mbe_enumerate": ([_P, ctypes.POINTER(Options), _P, ctypes.POINTER(Result), ctypes.POINTER(BicliqueBuffer)], _I32),
+    "mbe_release_workspace": ([], _I32),
+    "mbe_debug_trace": ([_P, _I32], _I32),
+    "mbe_copy_bandwidth": ([_I64, _I32, _P, ctypes.POINTER(ctypes.c_double)], _I32),
+    "mbe_enumerate_batch": ([_I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P, _P,
+                             ctypes.POINTER(Result)], _I32),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmbe.so (building it first when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise ImportError(f"CUDA library not built: {path}")
+            lib = ctypes.CDLL(path)
+            for name, (args, res) in _SIGNATURES.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def _check(st: int, what: str):
+    if st != MBE_OK:
+        raise MBEError(st, what)
+
+
+def _ptr(x):
+    """Raw pointer of a numpy array (host) or a torch tensor (device or host)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # noqa: BLE001
+            pass
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def options(**kw) -> Options:
+    o = Options()
+    _check(load().mbe_default_options(ctypes.byref(o)), "mbe_default_options")
+    for k, v in kw.items():
+        if k in ("per_root", "exec_order", "model"):
+            v = _ptr(v) if not isinstance(v, (int, type(None))) else v
+        setattr(o, k, v)
+    return o
+
+
+class Graph:
+    """A graph handle: wraps mbe_graph_create / mbe_enumerate / mbe_graph_destroy."""
+
+    def __init__(self, nU, nV, u_off, u_adj, v_off, v_adj, stream=None):
+        lib = load()
+        device = (not isinstance(u_off, np.ndarray)) and bool(getattr(u_off, "is_cuda", False))
+        if isinstance(u_off, np.ndarray):
+            u_off, u_adj, v_off, v_adj = (np.ascontiguousarray(a, dtype=np.int32) for a in (u_off, u_adj, v_off, v_adj))
+        self._keep = (u_off, u_adj, v_off, v_adj)
+        h = _P()
+        nE = int(u_adj.shape[0])
+        st = lib.mbe_graph_create(int(nU), int(nV), nE, _ptr(u_off), _ptr(u_adj), _ptr(v_off), _ptr(v_adj),
+                                  1 if device else 0, _stream_handle(stream), ctypes.byref(h))
+        _check(st, "mbe_graph_create")
+        self._h = h
+        self.nU, self.nV, self.nE = int(nU), int(nV), nE
+
+    @classmethod
+    def from_synth(cls, g, stream=None):
+        return cls(g.nU, g.nV, g.u_off, g.u_adj, g.v_off, g.v_adj, stream=stream)
+
+    def info(self):
+        vals = [ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()]
+        _check(load().mbe_graph_info(self._h, *[ctypes.byref(v) for v in vals]), "mbe_graph_info")
+        return dict(zip(("nU", "nV", "nE", "max_deg_u", "max_deg_v"), (v.value for v in vals)))
+
+    def enumerate(self, stream=None, bicliques=None, check=True, **kw) -> Result:
+        """Run mbe_enumerate; kw are mbe_options fields. bicliques: BicliqueBuffer or None."""
+        o = options(**kw)
+        r = Result()
+        st = load().mbe_enumerate(self._h, ctypes.byref(o), _stream_handle(stream), ctypes.byref(r),
+                                  ctypes.byref(bicliques) if bicliques is not None else None)
+        if check:
+            _check(st, "mbe_enumerate")
+        return r
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mbe_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def enumerate_batch(b, stream=None, check=True, **kw):
+    """mbe_enumerate_batch over a packed batch (host arrays). Returns (list of Result, total Result)."""
+    lib = load()
+    G = int(b.n_graphs)
+    arrs = [np.ascontiguousarray(b.edge_off, np.int64), np.ascontiguousarray(b.nU, np.int32),
+            np.ascontiguousarray(b.nV, np.int32), np.ascontiguousarray(b.u_off_start, np.int64),
+            np.ascontiguousarray(b.v_off_start, np.int64), np.ascontiguousarray(b.u_off, np.int32),
+            np.ascontiguousarray(b.u_adj, np.int32), np.ascontiguousarray(b.v_off, np.int32),
+            np.ascontiguousarray(b.v_adj, np.int32)]
+    per = (Result * max(G, 1))()
+    tot = Result()
+    o = options(**kw)
+    st = lib.mbe_enumerate_batch(G, *[a.ctypes.data for a in arrs], ctypes.byref(o), _stream_handle(stream),
+                                 ctypes.cast(per, _P), ctypes.byref(tot))
+    if check:
+        _check(st, "mbe_enumerate_batch")
+    return [per[i] for i in range(G)], tot
+
+
+def copy_bandwidth(nbytes: int, iters: int = 5, stream=None) -> float:
+    """Best device copy bandwidth in GB/s (read + write) over `iters` copies of `nbytes`."""
+    out = ctypes.c_double()
+    _check(load().mbe_copy_bandwidth(int(nbytes), int(iters), _stream_handle(stream), ctypes.byref(out)),
+           "mbe_copy_bandwidth")
+    return out.value
+
+
+def release_workspace():
+    _check(load().mbe_release_workspace(), "mbe_release_workspace")
+
+
+@dataclass
+class Bicliques:
+    """Device buffers for emitted bicliques plus the decoded host view."""
+
+    ids: object
+    offsets: object
+    buf: BicliqueBuffer
+
+    @classmethod
+    def allocate(cls, capacity_ids: int, capacity_bicliques: int):
+        import torch
+        ids = torch.empty(max(capacity_ids, 1), dtype=torch.int32, device="cuda")
+        offs = torch.empty(max(capacity_bicliques, 1), dtype=torch.int64, device="cuda")
+        buf = BicliqueBuffer(ids.data_ptr(), capacity_ids, offs.data_ptr(), capacity_bicliques, 0, 0)
+        return cls(ids, offs, buf)
+
+    def decode(self):
+        """List of (R, L) sorted tuples for the bicliques written."""
+        n = int(self.buf.n_bicliques_written)
+        ids = self.ids.cpu().numpy()
+        offs = self.offsets[:n].cpu().numpy()
+        out = []
+        for o in offs.tolist():
+            nr, nl = int(ids[o]), int(ids[o + 1])
+            r = tuple(sorted(ids[o + 2:o + 2 + nr].tolist()))
+            l = tuple(sorted(ids[o + 2 + nr:o + 2 + nr + nl].tolist()))
+            out.append((r, l))
+        return out

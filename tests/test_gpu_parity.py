@@ -1,0 +1,259 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Integer work, so the bar is bit-exact: count, hash, nodes and algorithmic
+bytes equal the oracle's, and on small graphs the sorted biclique set too.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from oracle.make_golden import expected_count
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mbe():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    import paper_2401_05039_gb300 as m
+    m.load()
+    return m
+
+
+def run(mbe, g, **kw):
+    G = mbe.Graph.from_synth(g)
+    try:
+        r = G.enumerate(**kw)
+    finally:
+        G.close()
+    return r
+
+
+def oracle_tuple(g):
+    return oracle.enumerate_graph(g)
+
+
+def gpu_tuple(r):
+    return (int(r.count), int(r.hash), int(r.nodes), int(r.bytes_alg))
+
+
+def test_er200x300_full_set(mbe, golden_dir):
+    import torch
+    g = synth.workload("er200x300")
+    with open(os.path.join(golden_dir, "er200x300.json")) as f:
+        gold = json.load(f)
+    assert g.digest() == gold["graph"]["digest"]
+    c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
+    G = mbe.Graph.from_synth(g)
+    buf = mbe.Bicliques.allocate(200000, 10000)
+    r = G.enumerate(emit=1, bicliques=buf.buf)
+    torch.cuda.synchronize()
+    assert gpu_tuple(r) == (c, h, n, b)
+    got = buf.decode()
+    assert len(got) == c
+    assert H.canon(got) == H.canon(rec)
+    G.close()
+
+
+def _random_cases(seed, n, max_expected=3000):
+    # sizes spanning several 32-row tiles with ragged tails; densities whose
+    # Bernoulli expected biclique count keeps the oracle at milliseconds
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < n:
+        nU = int(rng.integers(1, 120))
+        nV = int(rng.integers(1, 300))
+        p = float(rng.choice([0.02, 0.05, 0.1, 0.2, 0.35, 0.5]))
+        if expected_count(nU, nV, p) <= max_expected:
+            out.append(H.random_graph(rng, nU, nV, p))
+    return out
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_graphs_vs_oracle(mbe, seed):
+    for g in _random_cases(1000 + seed, 30):
+        assert gpu_tuple(run(mbe, g)) == oracle_tuple(g), (g.nU, g.nV, g.nE)
+
+
+def test_wide_rows_multiword(mbe):
+    # degrees near 90, 315 and 1100 give rows of 2, 5 and 18 words
+    rng = np.random.default_rng(7)
+    for nU, nV, p in [(16, 200, 0.45), (12, 700, 0.45), (12, 2000, 0.55)]:
+        g = H.random_graph(rng, nU, nV, p)
+        assert gpu_tuple(run(mbe, g)) == oracle_tuple(g), (nV, p)
+
+
+def test_closed_forms(mbe):
+    for a, b in [(1, 1), (3, 200), (70, 5), (40, 130)]:
+        r = run(mbe, H.complete(a, b))
+        assert r.count == 1 and r.nodes == a
+    for n in [1, 33, 100]:
+        assert run(mbe, H.matching(n)).count == n
+    for n in [3, 6, 10, 13]:
+        r = run(mbe, H.crown(n))
+        assert r.count == 2 ** n - 2
+        assert gpu_tuple(r) == oracle_tuple(H.crown(n))
+    r = run(mbe, H.empty(10, 10))
+    assert (r.count, r.hash, r.nodes) == (0, 0, 0)
+
+
+def test_emit_matches_closure(mbe):
+    import torch
+    rng = np.random.default_rng(9)
+    g = H.random_graph(rng, 60, 140, 0.15)
+    G = mbe.Graph.from_synth(g)
+    buf = mbe.Bicliques.allocate(500000, 50000)
+    r = G.enumerate(emit=1, bicliques=buf.buf)
+    torch.cuda.synchronize()
+    got = buf.decode()
+    adj = H.adjacency_sets(g)
+    assert len(got) == r.count == len(set(got))
+    assert all(H.is_closed_pair(g, R, L, adj) for R, L in got)
+    assert oracle.biclique_hash(got) == r.hash
+    G.close()
+
+
+def test_options_do_not_change_result(mbe):
+    g = synth.workload("er200x300")
+    base = gpu_tuple(run(mbe, g))
+    assert base == oracle_tuple(g)
+    for kw in [dict(steal=0), dict(block_threads=32, blocks_per_sm=1), dict(block_threads=1024, blocks_per_sm=1),
+               dict(block_threads=128, blocks_per_sm=4)]:
+        assert gpu_tuple(run(mbe, g, **kw)) == base, kw
+
+
+def test_explicit_orders_and_shards(mbe):
+    import torch
+    g = synth.workload("er200x300")
+    base = oracle_tuple(g)
+    live = np.nonzero(np.diff(g.u_off) > 0)[0].astype(np.int32)
+    rng = np.random.default_rng(3)
+    for order in [live, live[::-1].copy(), rng.permutation(live)]:
+        t = torch.from_numpy(np.ascontiguousarray(order)).cuda()
+        assert gpu_tuple(run(mbe, g, exec_order=t, n_exec=len(order))) == base
+    # shards of the execution order add up
+    G = mbe.Graph.from_synth(g)
+    n = len(live)
+    parts = [G.enumerate(root_begin=b, root_end=e) for b, e in [(0, 37), (37, 120), (120, n)]]
+    tot = (sum(p.count for p in parts), sum(p.hash for p in parts) % (1 << 64), sum(p.nodes for p in parts),
+           sum(p.bytes_alg for p in parts))
+    assert tot == base
+    G.close()
+
+
+def test_per_root_matches_oracle(mbe):
+    import torch
+    g = synth.workload("er200x300")
+    pr = oracle.per_root(g, nthreads=4)
+    G = mbe.Graph.from_synth(g)
+    buf = torch.zeros((g.nU, 4), dtype=torch.int64, device="cuda")
+    G.enumerate(per_root=buf)
+    got = buf.cpu().numpy().view(np.uint64)
+    assert (got == pr).all()
+    G.close()
+
+
+def _golden(golden_dir, name):
+    path = os.path.join(golden_dir, f"{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"no stored oracle values for {name}")
+    with open(path) as f:
+        return json.load(f)
+
+
+def _check_per_root_rows(mbe, g, gold, **kw):
+    import torch
+    G = mbe.Graph.from_synth(g)
+    buf = torch.zeros((g.nU, 4), dtype=torch.int64, device="cuda")
+    r = G.enumerate(per_root=buf, **kw)
+    got = buf.cpu().numpy().view(np.uint64)
+    for root, row in gold["per_root"].items():
+        u = int(root)
+        exp = (row["count"], int(row["hash"], 16), row["nodes"], row["bytes"])
+        assert tuple(int(x) for x in got[u]) == exp, (u, exp)
+    G.close()
+    return r, got
+
+
+def test_planted5k_totals(mbe, golden_dir):
+    gold = _golden(golden_dir, "planted5k")
+    g = synth.workload("planted5k")
+    assert g.digest() == gold["graph"]["digest"], "generator drew a different graph on this machine"
+    r, got = _check_per_root_rows(mbe, g, gold)
+    t = gold["total"]
+    assert gpu_tuple(r) == (t["count"], int(t["hash"], 16), t["nodes"], t["bytes"])
+    assert int(got[:, 0].sum()) == t["count"]
+
+
+def test_chunglu20k_roots(mbe, golden_dir):
+    # per-root rows of a seeded uniform prefix of the roots (their exact sum
+    # and individual rows); the whole-graph total when the oracle finished it
+    gold = _golden(golden_dir, "chunglu20k")
+    g = synth.workload("chunglu20k")
+    assert g.digest() == gold["graph"]["digest"], "generator drew a different graph on this machine"
+    r, got = _check_per_root_rows(mbe, g, gold)
+    pre = gold["prefix"]
+    live = np.nonzero(np.diff(g.u_off) > 0)[0]
+    perm = np.random.default_rng(pre["seed"]).permutation(live)[:pre["k"]]
+    s = got[perm].sum(axis=0, dtype=np.uint64)
+    exp = pre["sum"]
+    assert tuple(int(x) for x in s) == (exp["count"], int(exp["hash"], 16), exp["nodes"], exp["bytes"])
+    assert int(got[:, 0].sum()) == r.count and int(got[:, 2].sum()) == r.nodes
+    if gold.get("total"):
+        t = gold["total"]
+        assert gpu_tuple(r) == (t["count"], int(t["hash"], 16), t["nodes"], t["bytes"])
+
+
+def test_chunglu200k_sampled_roots(mbe, golden_dir):
+    gold = _golden(golden_dir, "chunglu200k")
+    g = synth.workload("chunglu200k")
+    assert g.digest() == gold["graph"]["digest"]
+    r, got = _check_per_root_rows(mbe, g, gold)
+    # whole-graph consistency: per-root rows add up to the totals
+    assert int(got[:, 0].sum()) == r.count
+    assert int(got[:, 2].sum()) == r.nodes
+
+
+def test_invalid_graphs_rejected(mbe):
+    g = H.random_graph(np.random.default_rng(1), 10, 12, 0.4)
+    bad = g.u_adj.copy()
+    seg = slice(int(g.u_off[2]), int(g.u_off[3]))
+    if bad[seg].size >= 2:
+        bad[seg] = bad[seg][::-1]
+    with pytest.raises(mbe.MBEError) as e:
+        mbe.Graph(g.nU, g.nV, g.u_off, bad, g.v_off, g.v_adj)
+    assert e.value.status == 2
+    vadj = g.v_adj.copy()
+    vadj[0] = (vadj[0] + 1) % g.nU
+    with pytest.raises(mbe.MBEError) as e:
+        mbe.Graph(g.nU, g.nV, g.u_off, g.u_adj, g.v_off, vadj)
+    assert e.value.status == 2
+
+
+def test_arena_overflow_is_reported_then_recovers(mbe):
+    g = synth.workload("er200x300")
+    G = mbe.Graph.from_synth(g)
+    r = G.enumerate(arena_bytes=256, check=False)
+    assert r.status == 4  # MBE_ERR_ARENA_FULL, no hang, no fault
+    r2 = G.enumerate()
+    assert gpu_tuple(r2) == oracle_tuple(g)
+    G.close()
+
+
+def test_watchdog_expires_cleanly(mbe):
+    # one worker holds the single heavy root while the others wait for work;
+    # a 1 ms watchdog makes their wait run out: the call returns
+    # MBE_ERR_TIMEOUT, and the next call with the default watchdog succeeds
+    g = H.crown(18)
+    G = mbe.Graph.from_synth(g)
+    r = G.enumerate(watchdog_ms=1, steal=0, check=False)
+    assert r.status == 6
+    r2 = G.enumerate()
+    assert r2.status == 0 and r2.count == 2 ** 18 - 2
+    G.close()
