@@ -178,7 +178,7 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
     const int64_t ncap = std::max<int64_t>(nc_max, 32);
     const int64_t urow = round_up(std::max<int64_t>(urow_max, 256), 256);
     const int64_t scratch = round_up(5 * round_up(4 * ncap, 16) + 16 * ncap + urow + 256, 256);
-    int64_t stack = stack_bytes_req > 0 ? stack_bytes_req : (int64_t)stack_factor * frame_max + (1 << 20);
+    int64_t stack = stack_bytes_req > 0 ? stack_bytes_req : (int64_t)stack_factor * frame_max + (256 << 10);
     stack = round_up(stack, 256);
     const int64_t arena = stack + scratch;
     const int64_t slot = round_up(std::max<int64_t>(frame_max, 4096), 256);
