@@ -5,4 +5,4 @@ The computation lives in the CUDA library built from ``csrc/`` (C ABI in
 """
 from . import build  # noqa: F401
 from .mbe import (Bicliques, BicliqueBuffer, Graph, MBEError, Options, Result, copy_bandwidth,  # noqa: F401
-                  enumerate_batch, library_path, load, options, release_workspace)
+                  enumerate_batch, enumerate_noalloc, library_path, load, options, release_workspace)
