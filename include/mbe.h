@@ -187,6 +187,30 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
                         const int32_t *u_adj_cat, const int32_t *v_off_cat, const int32_t *v_adj_cat,
                         const mbe_options *opts, void *stream, mbe_result *per_graph, mbe_result *total);
 
+/*
+ * Enumeration that allocates nothing (the paper has no counterpart; this is
+ * a deployment variant of mbe_enumerate). Some callers cannot call
+ * cudaMalloc: code inside a framework that owns all device memory through
+ * its own pool, where a raw allocation can fail or fragment that pool, and
+ * latency-critical loops that must not meet cudaMalloc/cudaFree (cudaFree
+ * synchronises the device). Such a caller passes its graph in its own
+ * DEVICE arrays (same layout and rules as mbe_graph_create) and receives
+ * count, hash, nodes and bytes_alg in the host struct *out (device_ms is -1:
+ * the call creates no timing events).
+ *
+ * Scratch: every call uses one fixed 64 MiB array compiled into the
+ * library (it exists on every GPU that loads the library until the process
+ * exits). A graph whose search workspace does not fit in it with at least
+ * one block of workers returns MBE_ERR_UNSUPPORTED; a search stack that
+ * outgrows its share returns MBE_ERR_ARENA_FULL (there is no retry). The
+ * first call on a device looks up the array's device address; make that
+ * first call before any stream capture. All calls on a device share the
+ * array: calls that overlap on the GPU race, so issue them one at a time.
+ * Returns an mbe_status like every entry point.
+ */
+int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const int32_t *u_off, const int32_t *u_adj,
+                          const int32_t *v_off, const int32_t *v_adj, void *stream, mbe_result *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,7 @@ _SIGNATURES = {
     "mbe_enumerate": ([_P, ctypes.POINTER(Options), _P, ctypes.POINTER(Result), ctypes.POINTER(BicliqueBuffer)], _I32),
     "mbe_release_workspace": ([], _I32),
     "mbe_debug_trace": ([_P, _I32], _I32),
+    "mbe_enumerate_noalloc": ([_I32, _I32, _I64, _P, _P, _P, _P, _P, ctypes.POINTER(Result)], _I32),
     "mbe_copy_bandwidth": ([_I64, _I32, _P, ctypes.POINTER(ctypes.c_double)], _I32),
     "mbe_enumerate_batch": ([_I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P, _P,
                              ctypes.POINTER(Result)], _I32),
@@ -203,6 +204,16 @@ def copy_bandwidth(nbytes: int, iters: int = 5, stream=None) -> float:
     _check(load().mbe_copy_bandwidth(int(nbytes), int(iters), _stream_handle(stream), ctypes.byref(out)),
            "mbe_copy_bandwidth")
     return out.value
+
+
+def enumerate_noalloc(nU, nV, u_off, u_adj, v_off, v_adj, stream=None, check=True) -> Result:
+    """mbe_enumerate_noalloc on DEVICE arrays (torch CUDA tensors); allocates nothing."""
+    r = Result()
+    st = load().mbe_enumerate_noalloc(int(nU), int(nV), int(u_adj.shape[0]), _ptr(u_off), _ptr(u_adj), _ptr(v_off),
+                                      _ptr(v_adj), _stream_handle(stream), ctypes.byref(r))
+    if check:
+        _check(st, "mbe_enumerate_noalloc")
+    return r
 
 
 def release_workspace():
