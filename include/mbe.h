@@ -124,6 +124,8 @@ typedef struct {
     int32_t *exec_order;      /* optional DEVICE array [nU]: explicit execution order of the roots
                                  (any permutation of a subset of U); overrides schedule */
     int32_t n_exec;           /* length of exec_order */
+    const void *class_params; /* mbe_enumerate_batch: const mbe_class_params[MBE_N_CLASSES] from
+                                 mbe_autotune_batch, or NULL for the defaults */
 } mbe_options;
 
 /* Fill *opt with the defaults (all "auto"). */
@@ -171,16 +173,48 @@ int mbe_enumerate(const mbe_graph *g, const mbe_options *opts, void *stream, mbe
                   mbe_biclique_buffer *bicliques);
 
 /*
+ * Batch size classes: graph (nU, nV, nE) falls in class
+ * 4*(nU >= 128) + 2*(nV >= 512) + (nE >= 0.1*nU*nV). Each class runs as one
+ * persistent launch with its own launch parameters.
+ */
+#define MBE_N_CLASSES 8
+
+typedef struct {
+    int32_t block_threads; /* 0 = default */
+    int32_t blocks_per_sm; /* 0 = default */
+    int32_t steal;         /* frame donation on/off for this class */
+    int32_t valid;         /* 0: the class uses the defaults */
+    double tuned_ms;       /* time the autotuner measured for this choice on its sample */
+} mbe_class_params;
+
+/* Size class of one graph (see MBE_N_CLASSES). */
+int mbe_batch_class(int32_t nU, int32_t nV, int64_t nE);
+
+/*
+ * Autotuner (no counterpart in the paper): for every size class present in
+ * the batch, times a set of launch shapes (block size, blocks per SM,
+ * stealing on/off) on an evenly spaced sample of the class (at least
+ * sample_per_class graphs and enough graphs for 16 roots per worker, or the
+ * whole class) and writes the fastest into table[class] (valid = 1).
+ * Arguments as in mbe_enumerate_batch; table has MBE_N_CLASSES entries.
+ */
+int mbe_autotune_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t *nU, const int32_t *nV,
+                       const int64_t *u_off_start, const int64_t *v_off_start, const int32_t *u_off_cat,
+                       const int32_t *u_adj_cat, const int32_t *v_off_cat, const int32_t *v_adj_cat,
+                       int32_t sample_per_class, void *stream, mbe_class_params *table);
+
+/*
  * Enumerate many independent graphs in one call. Graph i has nU[i] x nV[i]
  * vertices, its edges are positions [edge_off[i], edge_off[i+1]) of the
  * concatenated u_adj_cat / v_adj_cat (ids local to the graph), and its
  * offset arrays start at u_off_cat[u_off_start[i]] (nU[i]+1 entries,
  * local, starting at 0) and v_off_cat[v_off_start[i]] (nV[i]+1 entries).
- * All arrays are HOST memory. per_graph[i] receives graph i's result.
- * Graphs are binned into size classes; each class runs with parameters
- * chosen by the autotuner (mbe_autotune) when a table is loaded, else
- * with defaults; the class launches are captured in one CUDA graph.
- * Limits: per graph nU <= 65536 and every degree <= 64 * 32.
+ * All arrays are HOST memory. per_graph[i] receives graph i's result;
+ * total the sums and the device time of the whole batch. Graphs are binned
+ * into size classes; each class is one persistent launch over its (graph,
+ * root) tasks with the parameters of opts->class_params (autotuned) or the
+ * defaults; the launches of all classes are captured in one CUDA graph and
+ * replayed. Limits: per graph nU <= 65536 and every degree <= 2048.
  */
 int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t *nU, const int32_t *nV,
                         const int64_t *u_off_start, const int64_t *v_off_start, const int32_t *u_off_cat,

@@ -11,49 +11,7 @@
 #include "../../include/mbe.h"
 #include "mbe_internal.h"
 #include "mbe_prep.h"
-
-namespace mbe {
-
-// Device-side control block of one search launch (zeroed before each launch).
-struct Ctl {
-    unsigned long long cursor;
-    long long outstanding;
-    int32_t n_idle;
-    int32_t error;
-    int32_t n_published;
-    int32_t pad;
-    unsigned long long totals[8];
-    unsigned long long used_ids;
-    unsigned long long used_bic;
-};
-
-struct Workspace {
-    char *arena = nullptr;
-    int64_t arena_bytes = 0, scratch_bytes = 0;
-    char *slots = nullptr;
-    int64_t slot_bytes = 0;
-    int32_t *slot_state = nullptr;
-    int32_t *mark = nullptr;
-    int64_t mark_stride = 0;
-    int n_warps = 0;
-    int threads = 0, blocks = 0;
-    Ctl *ctl = nullptr;
-    int64_t n_cand_cap = 0, urow_bytes = 0;
-    bool marks_dirty = false;
-    bool budget_limited = false; // fewer warps than requested because of device memory
-
-    void release()
-    {
-        cudaFree(arena);
-        cudaFree(slots);
-        cudaFree(slot_state);
-        cudaFree(mark);
-        cudaFree(ctl);
-        *this = Workspace();
-    }
-};
-
-} // namespace mbe
+#include "mbe_runtime.h"
 
 struct mbe_graph {
     int device = 0;
@@ -69,12 +27,13 @@ struct mbe_graph {
 };
 
 namespace mbe {
-namespace {
 
 // Search workspace shared by every call on a device (grown on demand, kept
 // until mbe_release_workspace or process exit).
+namespace {
 constexpr int kMaxDevices = 64;
 Workspace g_ws[kMaxDevices];
+} // namespace
 
 Workspace &device_workspace()
 {
@@ -119,8 +78,10 @@ long long deadline_ms()
 }
 
 // Per-worker progress records when MBE_DEBUG_TRACE is set (dumped with mbe_debug_trace).
+namespace {
 unsigned long long *g_debug = nullptr;
 int g_debug_warps = 0;
+} // namespace
 unsigned long long *debug_buffer(int n_warps)
 {
     if (!getenv("MBE_DEBUG_TRACE")) return nullptr;
@@ -145,22 +106,18 @@ int key_bits_for(int64_t n)
     return b;
 }
 
-struct LaunchShape {
-    int threads, blocks, warps;
-};
-
-LaunchShape choose_shape(const mbe_options &o)
+LaunchShape shape_for(int block_threads, int blocks_per_sm)
 {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int threads = o.block_threads > 0 ? o.block_threads : 256;
+    int threads = block_threads > 0 ? block_threads : 256;
     threads = std::max(32, std::min(1024, threads / 32 * 32));
-    int per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : std::max(1, 512 / threads); // 16 warps per SM by default
+    int per_sm = blocks_per_sm > 0 ? blocks_per_sm : std::max(1, 512 / threads); // 16 warps per SM by default
     int fit = search_fit_shape(threads, per_sm);
     if (fit < 0) { // block too large for the kernel's register use
         threads = -fit;
-        per_sm = o.blocks_per_sm > 0 ? o.blocks_per_sm : std::max(1, 512 / threads);
+        per_sm = blocks_per_sm > 0 ? blocks_per_sm : std::max(1, 512 / threads);
         fit = search_fit_shape(threads, per_sm);
     }
     if (fit > 0) per_sm = fit;
@@ -170,6 +127,8 @@ LaunchShape choose_shape(const mbe_options &o)
     s.warps = s.blocks * (threads / 32);
     return s;
 }
+
+LaunchShape choose_shape(const mbe_options &o) { return shape_for(o.block_threads, o.blocks_per_sm); }
 
 // Sizes (and allocates when needed) the per-warp workspace for a launch.
 int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t frame_max, int32_t max_nU,
@@ -190,9 +149,8 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
     const int64_t per_warp = arena + slot + 4 * mark_stride + 4;
     // an existing workspace is reused when every region is large enough; the
     // scratch split is recomputed for this graph inside the same arena
-    const bool fits_current = ws.arena && ws.threads == shape.threads && ws.arena_bytes >= arena &&
-                              ws.slot_bytes >= slot && ws.mark_stride >= mark_stride &&
-                              (ws.n_warps == n_warps || ws.budget_limited);
+    const bool fits_current = ws.arena && ws.arena_bytes >= arena && ws.slot_bytes >= slot &&
+                              ws.mark_stride >= mark_stride && (ws.n_warps >= n_warps || ws.budget_limited);
     if (fits_current) {
         ws.scratch_bytes = scratch;
         ws.n_cand_cap = ncap;
@@ -239,18 +197,6 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
     return MBE_OK;
 }
 
-struct RunInput {
-    const int32_t *u_off, *u_adj, *v_off, *v_adj;
-    const GraphDesc *d_desc;
-    int32_t n_graphs;
-    int32_t max_nU;
-    const int32_t *task_root, *task_graph;
-    int64_t n_tasks;
-    int64_t nc_max, urow_max, frame_max;
-    unsigned long long *per_owner; // [n_owner][4], zeroed here before every launch
-    int64_t n_owner;
-    int32_t per_mode;
-};
 
 // One persistent search launch (with automatic arena growth on overflow).
 int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStream_t s, mbe_result *out,
@@ -303,7 +249,9 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         a.n_published = &ws.ctl->n_published;
         a.debug = debug_buffer(ws.n_warps);
         a.steal = o.steal ? 1 : 0;
-        a.n_warps = ws.n_warps;
+        const int wpb = shape.threads / 32;
+        const int blocks = std::min(shape.blocks, ws.n_warps / wpb);
+        a.n_warps = blocks * wpb;
         a.max_words = o.bitset_max_words > 0 ? std::min(o.bitset_max_words, 32) : 32;
         a.totals = ws.ctl->totals;
         a.per_task_owner = in.per_owner;
@@ -321,7 +269,7 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         MBE_TRY(cudaEventCreate(&e0));
         MBE_TRY(cudaEventCreate(&e1));
         cudaEventRecord(e0, s);
-        cudaError_t le = launch_search(a, ws.blocks, ws.threads, s);
+        cudaError_t le = launch_search(a, blocks, shape.threads, s);
         cudaEventRecord(e1, s);
         Ctl h;
         cudaError_t ce = cudaMemcpyAsync(&h, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
@@ -345,7 +293,7 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
             out->bytes_alg = h.totals[3];
             out->n_donations = h.totals[4];
             out->device_ms = ms;
-            out->n_workers = ws.n_warps;
+            out->n_workers = a.n_warps;
         }
         if (a.emit) {
             bic->n_ids_written = (int64_t)h.used_ids;
@@ -356,7 +304,6 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
     return MBE_ERR_ARENA_FULL;
 }
 
-} // namespace
 } // namespace mbe
 
 using namespace mbe;
@@ -581,172 +528,6 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     in.per_mode = 1;
     int st = run_search(device_workspace(), in, o, s, out, bicliques);
     return set_status(out, st);
-}
-
-int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t *nU, const int32_t *nV,
-                        const int64_t *u_off_start, const int64_t *v_off_start, const int32_t *u_off_cat,
-                        const int32_t *u_adj_cat, const int32_t *v_off_cat, const int32_t *v_adj_cat,
-                        const mbe_options *opts, void *stream, mbe_result *per_graph, mbe_result *total)
-{
-    if (total) memset(total, 0, sizeof(*total));
-    if (n_graphs < 0 || (n_graphs > 0 && (!edge_off || !nU || !nV || !u_off_start || !v_off_start || !u_off_cat ||
-                                          !v_off_cat || !per_graph)))
-        return set_status(total, MBE_ERR_INVALID_ARG);
-    if (n_graphs == 0) return set_status(total, MBE_OK);
-    mbe_options o;
-    mbe_default_options(&o);
-    if (opts) o = *opts;
-    o.emit = 0;
-    cudaStream_t s = (cudaStream_t)stream;
-
-    // host-side descriptors and the task list (graphs by falling density x size, roots by falling degree)
-    std::vector<GraphDesc> desc((size_t)n_graphs);
-    int64_t n_uoff = 0, n_voff = 0, nE = edge_off[n_graphs];
-    int32_t max_nU = 1;
-    for (int32_t i = 0; i < n_graphs; ++i) {
-        if (nU[i] < 0 || nV[i] < 0 || nU[i] > 65536 || edge_off[i + 1] < edge_off[i])
-            return set_status(total, MBE_ERR_INVALID_ARG);
-        desc[i] = GraphDesc{u_off_start[i], v_off_start[i], edge_off[i], nU[i], nV[i]};
-        n_uoff = std::max<int64_t>(n_uoff, u_off_start[i] + nU[i] + 1);
-        n_voff = std::max<int64_t>(n_voff, v_off_start[i] + nV[i] + 1);
-        max_nU = std::max(max_nU, nU[i]);
-    }
-    if (nE > 0 && (!u_adj_cat || !v_adj_cat)) return set_status(total, MBE_ERR_INVALID_ARG);
-    for (int32_t i = 0; i < n_graphs; ++i) {
-        const int32_t *uo = u_off_cat + u_off_start[i];
-        const int32_t *vo = v_off_cat + v_off_start[i];
-        if (uo[0] != 0 || vo[0] != 0 || (int64_t)uo[nU[i]] != edge_off[i + 1] - edge_off[i] ||
-            (int64_t)vo[nV[i]] != edge_off[i + 1] - edge_off[i])
-            return set_status(total, MBE_ERR_INVALID_GRAPH);
-        for (int32_t u = 0; u < nU[i]; ++u)
-            if ((uo[u + 1] - uo[u]) > 64 * 32) return set_status(total, MBE_ERR_UNSUPPORTED);
-    }
-    std::vector<int32_t> gorder((size_t)n_graphs);
-    for (int32_t i = 0; i < n_graphs; ++i) gorder[i] = i;
-    std::vector<double> gkey((size_t)n_graphs);
-    for (int32_t i = 0; i < n_graphs; ++i) {
-        double ne = (double)(edge_off[i + 1] - edge_off[i]);
-        double dens = (nU[i] && nV[i]) ? ne / ((double)nU[i] * nV[i]) : 0.0;
-        gkey[i] = ne * dens * dens;
-    }
-    std::stable_sort(gorder.begin(), gorder.end(), [&](int32_t a, int32_t b) { return gkey[a] > gkey[b]; });
-    std::vector<int32_t> troot, tgraph;
-    troot.reserve((size_t)n_uoff);
-    tgraph.reserve((size_t)n_uoff);
-    std::vector<std::pair<int32_t, int32_t>> tmp;
-    for (int32_t gi : gorder) {
-        const int32_t *uo = u_off_cat + u_off_start[gi];
-        tmp.clear();
-        for (int32_t u = 0; u < nU[gi]; ++u) {
-            int32_t d = uo[u + 1] - uo[u];
-            if (d > 0) tmp.push_back({-d, u});
-        }
-        std::sort(tmp.begin(), tmp.end());
-        for (auto &p : tmp) {
-            troot.push_back(p.second);
-            tgraph.push_back(gi);
-        }
-    }
-    const int64_t n_tasks = (int64_t)troot.size();
-
-    int32_t *d_uo = nullptr, *d_vo = nullptr, *d_ua = nullptr, *d_va = nullptr, *d_tr = nullptr, *d_tg = nullptr,
-            *d_bad = nullptr;
-    GraphDesc *d_desc = nullptr;
-    unsigned long long *d_bounds = nullptr, *d_owner = nullptr;
-    Workspace &ws = device_workspace();
-    int st = MBE_OK;
-    auto cleanup = [&]() {
-        cudaFree(d_uo);
-        cudaFree(d_vo);
-        cudaFree(d_ua);
-        cudaFree(d_va);
-        cudaFree(d_tr);
-        cudaFree(d_tg);
-        cudaFree(d_bad);
-        cudaFree(d_desc);
-        cudaFree(d_bounds);
-        cudaFree(d_owner);
-    };
-    const size_t eb = sizeof(int32_t) * (size_t)std::max<int64_t>(nE, 1);
-    if (cudaMalloc(&d_uo, sizeof(int32_t) * (size_t)n_uoff) != cudaSuccess ||
-        cudaMalloc(&d_vo, sizeof(int32_t) * (size_t)n_voff) != cudaSuccess || cudaMalloc(&d_ua, eb) != cudaSuccess ||
-        cudaMalloc(&d_va, eb) != cudaSuccess ||
-        cudaMalloc(&d_tr, sizeof(int32_t) * (size_t)std::max<int64_t>(n_tasks, 1)) != cudaSuccess ||
-        cudaMalloc(&d_tg, sizeof(int32_t) * (size_t)std::max<int64_t>(n_tasks, 1)) != cudaSuccess ||
-        cudaMalloc(&d_bad, sizeof(int32_t)) != cudaSuccess ||
-        cudaMalloc(&d_desc, sizeof(GraphDesc) * (size_t)n_graphs) != cudaSuccess ||
-        cudaMalloc(&d_bounds, sizeof(unsigned long long) * 8) != cudaSuccess ||
-        cudaMalloc(&d_owner, sizeof(unsigned long long) * 4 * (size_t)n_graphs) != cudaSuccess) {
-        cudaGetLastError();
-        cleanup();
-        return set_status(total, MBE_ERR_OOM);
-    }
-    cudaError_t e = cudaMemcpyAsync(d_uo, u_off_cat, sizeof(int32_t) * (size_t)n_uoff, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_vo, v_off_cat, sizeof(int32_t) * (size_t)n_voff, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && nE > 0) e = cudaMemcpyAsync(d_ua, u_adj_cat, eb, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && nE > 0) e = cudaMemcpyAsync(d_va, v_adj_cat, eb, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_tasks > 0)
-        e = cudaMemcpyAsync(d_tr, troot.data(), sizeof(int32_t) * (size_t)n_tasks, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n_tasks > 0)
-        e = cudaMemcpyAsync(d_tg, tgraph.data(), sizeof(int32_t) * (size_t)n_tasks, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(d_desc, desc.data(), sizeof(GraphDesc) * (size_t)n_graphs, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_bounds, 0, sizeof(unsigned long long) * 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d_owner, 0, sizeof(unsigned long long) * 4 * (size_t)n_graphs, s);
-    for (int32_t i = 0; i < n_graphs && e == cudaSuccess; ++i)
-        e = validate_graph(d_uo + u_off_start[i], d_ua + edge_off[i], d_vo + v_off_start[i], d_va + edge_off[i],
-                           nU[i], nV[i], edge_off[i + 1] - edge_off[i], d_bad, s);
-    if (e == cudaSuccess) e = root_bounds(d_desc, n_graphs, max_nU, d_uo, d_ua, d_vo, d_bounds, s);
-    unsigned long long hb[8] = {0};
-    int32_t hbad = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, d_bounds, sizeof(hb), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        cleanup();
-        return set_status(total, cuda_status(e));
-    }
-    if (hbad) {
-        cleanup();
-        return set_status(total, MBE_ERR_INVALID_GRAPH);
-    }
-    RunInput in;
-    in.u_off = d_uo;
-    in.u_adj = d_ua;
-    in.v_off = d_vo;
-    in.v_adj = d_va;
-    in.d_desc = d_desc;
-    in.n_graphs = n_graphs;
-    in.max_nU = max_nU;
-    in.task_root = d_tr;
-    in.task_graph = d_tg;
-    in.n_tasks = n_tasks;
-    in.nc_max = (int64_t)hb[0];
-    in.urow_max = (int64_t)hb[1];
-    in.frame_max = (int64_t)hb[2];
-    in.per_owner = d_owner;
-    in.n_owner = n_graphs;
-    in.per_mode = 2;
-    st = n_tasks > 0 ? run_search(ws, in, o, s, total, nullptr) : MBE_OK;
-    std::vector<unsigned long long> res((size_t)n_graphs * 4);
-    if (st == MBE_OK || st == MBE_ERR_TIMEOUT) {
-        e = cudaMemcpy(res.data(), d_owner, sizeof(unsigned long long) * 4 * (size_t)n_graphs, cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) st = cuda_status(e);
-    }
-    for (int32_t i = 0; i < n_graphs; ++i) {
-        mbe_result &r = per_graph[i];
-        memset(&r, 0, sizeof(r));
-        r.count = res[4 * i + 0];
-        r.hash = res[4 * i + 1];
-        r.nodes = res[4 * i + 2];
-        r.bytes_alg = res[4 * i + 3];
-        r.status = st;
-    }
-    cleanup();
-    return set_status(total, st);
 }
 
 } // extern "C"

@@ -3,6 +3,8 @@
 #include "mbe_internal.h"
 #include "mbe_prep.h"
 
+#include <algorithm>
+
 namespace mbe {
 namespace {
 
@@ -156,6 +158,92 @@ __global__ void key_scatter_kernel(const int32_t *key, int32_t n, int32_t *pos, 
         if (key[u] >= 0) order[atomicAdd(pos + key[u], 1)] = u;
 }
 
+// Batched validation: grid.y = graph. Same checks as validate_csr_kernel and
+// validate_transpose_kernel for every graph of a concatenated batch.
+__global__ void validate_batch_kernel(const GraphDesc *graphs, const int32_t *u_off_cat, const int32_t *u_adj_cat,
+                                      const int32_t *v_off_cat, const int32_t *v_adj_cat, int32_t *bad)
+{
+    const GraphDesc G = graphs[blockIdx.y];
+    const int32_t *uo = u_off_cat + G.u_off_base, *vo = v_off_cat + G.v_off_base;
+    const int32_t *ua = u_adj_cat + G.edge_base, *va = v_adj_cat + G.edge_base;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (t == 0 && (uo[0] != 0 || vo[0] != 0 || uo[G.nU] != vo[G.nV])) atomicOr(bad, 1);
+    const int nE = uo[G.nU];
+    for (int u = t; u < G.nU; u += stride) {
+        int a = uo[u], b = uo[u + 1], prev = -1;
+        if (b < a || a < 0 || b > nE) {
+            atomicOr(bad, 4);
+            continue;
+        }
+        for (int k = a; k < b; ++k) {
+            int v = ua[k];
+            if (v <= prev || v >= G.nV) {
+                atomicOr(bad, 8);
+                break;
+            }
+            prev = v;
+            int lo = vo[v], hi = vo[v + 1];
+            while (lo < hi) {
+                int mid = lo + ((hi - lo) >> 1);
+                if (va[mid] < u) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo >= vo[v + 1] || va[lo] != u) {
+                atomicOr(bad, 16);
+                break;
+            }
+        }
+    }
+    for (int v = t; v < G.nV; v += stride) {
+        int a = vo[v], b = vo[v + 1], prev = -1;
+        if (b < a || a < 0 || b > nE) {
+            atomicOr(bad, 4);
+            continue;
+        }
+        for (int k = a; k < b; ++k) {
+            if (va[k] <= prev || va[k] >= G.nU) {
+                atomicOr(bad, 8);
+                break;
+            }
+            prev = va[k];
+        }
+    }
+}
+
+// Per-graph workspace bounds: out[4g..4g+3] = max over the roots of graph g
+// of (candidates, universe row bytes, level-1 frame bytes, degree); same
+// per-root bounds as root_bounds_kernel.
+__global__ void graph_bounds_kernel(const GraphDesc *graphs, const int32_t *u_off_cat, const int32_t *u_adj_cat,
+                                    const int32_t *v_off_cat, unsigned long long *out)
+{
+    const int g = blockIdx.y;
+    const GraphDesc G = graphs[g];
+    const int32_t *u_off = u_off_cat + G.u_off_base, *v_off = v_off_cat + G.v_off_base;
+    const int32_t *u_adj = u_adj_cat + G.edge_base;
+    unsigned long long m_nc = 0, m_urow = 0, m_frame = 0, m_deg = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < G.nU; r += gridDim.x * blockDim.x) {
+        int a = u_off[r], d = u_off[r + 1] - a;
+        if (d == 0) continue;
+        long long s = 0;
+        for (int k = 0; k < d; ++k) {
+            int w = u_adj[a + k];
+            s += v_off[w + 1] - v_off[w] - 1;
+        }
+        long long nc = s < (long long)G.nU - 1 ? s : (long long)G.nU - 1;
+        long long W = (d + 63) / 64, tiles = (nc + 31) / 32;
+        unsigned long long urow = 256ULL * W * tiles;
+        unsigned long long frame = 64 + ((4ULL * d + 15) & ~15ULL) + 2 * ((4ULL * nc + 15) & ~15ULL) + urow + 16;
+        m_nc = max(m_nc, (unsigned long long)nc);
+        m_urow = max(m_urow, urow);
+        m_frame = max(m_frame, frame);
+        m_deg = max(m_deg, (unsigned long long)d);
+    }
+    atomicMax(out + 4LL * g + 0, m_nc);
+    atomicMax(out + 4LL * g + 1, m_urow);
+    atomicMax(out + 4LL * g + 2, m_frame);
+    atomicMax(out + 4LL * g + 3, m_deg);
+}
+
 __global__ void max_degree_kernel(const int32_t *off, int32_t n, int32_t *out)
 {
     int m = 0;
@@ -165,6 +253,26 @@ __global__ void max_degree_kernel(const int32_t *off, int32_t n, int32_t *out)
 }
 
 } // namespace
+
+cudaError_t validate_batch(const GraphDesc *d_graphs, int32_t n_graphs, const int32_t *u_off, const int32_t *u_adj,
+                           const int32_t *v_off, const int32_t *v_adj, int32_t *d_bad, cudaStream_t s)
+{
+    for (int32_t g0 = 0; g0 < n_graphs; g0 += 65535) {
+        dim3 grid(2, std::min<int32_t>(65535, n_graphs - g0));
+        validate_batch_kernel<<<grid, 256, 0, s>>>(d_graphs + g0, u_off, u_adj, v_off, v_adj, d_bad);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t graph_bounds(const GraphDesc *d_graphs, int32_t n_graphs, const int32_t *u_off, const int32_t *u_adj,
+                         const int32_t *v_off, unsigned long long *d_out, cudaStream_t s)
+{
+    for (int32_t g0 = 0; g0 < n_graphs; g0 += 65535) {
+        dim3 grid(2, std::min<int32_t>(65535, n_graphs - g0));
+        graph_bounds_kernel<<<grid, 256, 0, s>>>(d_graphs + g0, u_off, u_adj, v_off, d_out + 4LL * g0);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t max_degree(const int32_t *off, int32_t n, int32_t *d_out, cudaStream_t s)
 {

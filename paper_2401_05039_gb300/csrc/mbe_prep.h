@@ -11,6 +11,15 @@ namespace mbe {
 cudaError_t validate_graph(const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off, const int32_t *v_adj,
                            int32_t nU, int32_t nV, int64_t nE, int32_t *d_bad, cudaStream_t s);
 
+// Every graph of a concatenated batch checked in one launch (ORs into *d_bad).
+cudaError_t validate_batch(const GraphDesc *d_graphs, int32_t n_graphs, const int32_t *u_off, const int32_t *u_adj,
+                           const int32_t *v_off, const int32_t *v_adj, int32_t *d_bad, cudaStream_t s);
+
+// d_out[4g..4g+3] (zeroed by the caller): max candidates, universe bytes,
+// level-1 frame bytes and degree over the roots of graph g.
+cudaError_t graph_bounds(const GraphDesc *d_graphs, int32_t n_graphs, const int32_t *u_off, const int32_t *u_adj,
+                         const int32_t *v_off, unsigned long long *d_out, cudaStream_t s);
+
 // *d_out = max(*d_out, largest list length of the CSR off[0..n]).
 cudaError_t max_degree(const int32_t *off, int32_t n, int32_t *d_out, cudaStream_t s);
 

@@ -1217,9 +1217,18 @@ int search_fit_shape(int threads, int blocks_per_sm_req)
 
 cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
 {
-    int smem = (threads / 32) * search_smem_per_warp();
-    cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
+    // the dynamic shared memory limit is raised once to the largest block
+    // (no attribute calls between captured launches)
+    static int smem_set[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int smem = (threads / 32) * search_smem_per_warp();
+    if (dev >= 0 && dev < 64 && smem_set[dev] < 32 * search_smem_per_warp()) {
+        cudaError_t e = cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             32 * search_smem_per_warp());
+        if (e != cudaSuccess) return e;
+        smem_set[dev] = 32 * search_smem_per_warp();
+    }
     search_kernel<<<blocks, threads, smem, stream>>>(a);
     return cudaGetLastError();
 }

@@ -36,7 +36,16 @@ class Options(ctypes.Structure):
                 ("bitset_max_words", ctypes.c_int32), ("steal", ctypes.c_int32), ("schedule", ctypes.c_int32),
                 ("emit", ctypes.c_int32), ("watchdog_ms", ctypes.c_int32), ("root_begin", ctypes.c_int32),
                 ("root_end", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("model", ctypes.c_void_p),
-                ("per_root", ctypes.c_void_p), ("exec_order", ctypes.c_void_p), ("n_exec", ctypes.c_int32)]
+                ("per_root", ctypes.c_void_p), ("exec_order", ctypes.c_void_p), ("n_exec", ctypes.c_int32),
+                ("class_params", ctypes.c_void_p)]
+
+
+class ClassParams(ctypes.Structure):
+    _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("steal", ctypes.c_int32),
+                ("valid", ctypes.c_int32), ("tuned_ms", ctypes.c_double)]
+
+
+N_CLASSES = 8
 
 
 class Result(ctypes.Structure):
@@ -69,6 +78,8 @@ _SIGNATURES = {
     "mbe_debug_trace": ([_P, _I32], _I32),
     "mbe_enumerate_noalloc": ([_I32, _I32, _I64, _P, _P, _P, _P, _P, ctypes.POINTER(Result)], _I32),
     "mbe_copy_bandwidth": ([_I64, _I32, _P, ctypes.POINTER(ctypes.c_double)], _I32),
+    "mbe_batch_class": ([_I32, _I32, _I64], _I32),
+    "mbe_autotune_batch": ([_I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I32, _P, _P], _I32),
     "mbe_enumerate_batch": ([_I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P, _P,
                              ctypes.POINTER(Result)], _I32),
 }
@@ -125,7 +136,9 @@ def options(**kw) -> Options:
     o = Options()
     _check(load().mbe_default_options(ctypes.byref(o)), "mbe_default_options")
     for k, v in kw.items():
-        if k in ("per_root", "exec_order", "model"):
+        if k == "class_params" and v is not None and not isinstance(v, int):
+            v = ctypes.cast(v, ctypes.c_void_p).value
+        elif k in ("per_root", "exec_order", "model"):
             v = _ptr(v) if not isinstance(v, (int, type(None))) else v
         setattr(o, k, v)
     return o
@@ -179,15 +192,32 @@ class Graph:
             pass
 
 
-def enumerate_batch(b, stream=None, check=True, **kw):
-    """mbe_enumerate_batch over a packed batch (host arrays). Returns (list of Result, total Result)."""
-    lib = load()
-    G = int(b.n_graphs)
-    arrs = [np.ascontiguousarray(b.edge_off, np.int64), np.ascontiguousarray(b.nU, np.int32),
+def _batch_arrays(b):
+    return [np.ascontiguousarray(b.edge_off, np.int64), np.ascontiguousarray(b.nU, np.int32),
             np.ascontiguousarray(b.nV, np.int32), np.ascontiguousarray(b.u_off_start, np.int64),
             np.ascontiguousarray(b.v_off_start, np.int64), np.ascontiguousarray(b.u_off, np.int32),
             np.ascontiguousarray(b.u_adj, np.int32), np.ascontiguousarray(b.v_off, np.int32),
             np.ascontiguousarray(b.v_adj, np.int32)]
+
+
+def batch_class(nU, nV, nE) -> int:
+    return int(load().mbe_batch_class(int(nU), int(nV), int(nE)))
+
+
+def autotune_batch(b, sample_per_class=64, stream=None):
+    """mbe_autotune_batch: returns the per-class parameter table (ClassParams * N_CLASSES)."""
+    table = (ClassParams * N_CLASSES)()
+    arrs = _batch_arrays(b)
+    _check(load().mbe_autotune_batch(int(b.n_graphs), *[a.ctypes.data for a in arrs], int(sample_per_class),
+                                     _stream_handle(stream), ctypes.cast(table, _P)), "mbe_autotune_batch")
+    return table
+
+
+def enumerate_batch(b, stream=None, check=True, **kw):
+    """mbe_enumerate_batch over a packed batch (host arrays). Returns (list of Result, total Result)."""
+    lib = load()
+    G = int(b.n_graphs)
+    arrs = _batch_arrays(b)
     per = (Result * max(G, 1))()
     tot = Result()
     o = options(**kw)

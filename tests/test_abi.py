@@ -106,3 +106,12 @@ int main(){unsigned long long z=0x1234567ULL;for(int i=0;i<100000;i++){z=z*63641
         z = (z * 6364136223846793005 + 1442695040888963407) & M
         exp.append(oracle.sm(z))
     assert got == exp
+
+
+def test_batch_size_classes():
+    import paper_2401_05039_gb300 as m
+    assert m.batch_class(16, 16, 10) == 0
+    assert m.batch_class(16, 16, 100) == 1          # density >= 0.1
+    assert m.batch_class(200, 16, 10) == 4
+    assert m.batch_class(16, 600, 10) == 2
+    assert m.batch_class(512, 2048, 200000) == 7
