@@ -104,6 +104,54 @@ int mbe_release_workspace(void);
  */
 int mbe_copy_bandwidth(int64_t bytes, int32_t iters, void *stream, double *gbps);
 
+/* ------------------------------------------------------------ cost model */
+/*
+ * The learned schedule (no counterpart in the paper; it feeds Section III-C's
+ * task distribution). A small network predicts log(1 + nodes of a root's
+ * subtree) from eight per-root features; mbe_enumerate with schedule = 1
+ * runs the roots heaviest-predicted first and splits the heaviest into
+ * several tasks. Counts, hashes and nodes never depend on it.
+ */
+typedef struct mbe_model mbe_model;
+
+/* Parameters: W1[64][8], b1[64], W2[64][64], b2[64], W3[64], b3 (float32 master copy). */
+#define MBE_MODEL_PARAMS 4801
+#define MBE_N_FEATURES 8
+
+/* Network with Uniform(+-1/sqrt(fan_in)) weights (SplitMix64 stream of seed) and zero biases. */
+int mbe_model_create(uint64_t seed, mbe_model **out);
+int mbe_model_destroy(mbe_model *m);
+/* Copy MBE_MODEL_PARAMS floats in / out (HOST memory); set also clears the optimiser state. */
+int mbe_model_set_params(mbe_model *m, const float *host_params);
+int mbe_model_get_params(const mbe_model *m, float *host_params);
+
+/*
+ * Per-root features of every U vertex (DEVICE outputs, [nU][8]): log1p of
+ * degree, |N2(r)|, |P0| (later in (degree, id) order), |Q0| (earlier), core
+ * number of G as a general graph, sum and max of the neighbours' degrees,
+ * and the fraction of U vertices of larger degree; all zero for isolated
+ * vertices. d_raw (may be NULL) receives the integer values before log1p.
+ */
+int mbe_root_features(const mbe_graph *g, float *d_feat, int32_t *d_raw, void *stream);
+
+/* Forward pass: d_out[i] = prediction for d_feat[i][0..7] (FP16 operands, FP32 accumulation). */
+int mbe_model_predict(const mbe_model *m, const float *d_feat, int32_t n, float *d_out, void *stream);
+
+/*
+ * Mean squared error of the predictions for n rows against d_target (DEVICE)
+ * and its gradient with respect to the parameters (HOST output, 4801 floats).
+ */
+int mbe_model_loss_grad(mbe_model *m, const float *d_feat, const float *d_target, int32_t n, float *host_grad,
+                        float *host_loss, void *stream);
+
+/*
+ * Adam training on the GPU: `epochs` passes over n rows (DEVICE features and
+ * targets) in shuffled minibatches of `batch`; *final_loss is the mean
+ * minibatch loss of the last epoch.
+ */
+int mbe_model_train(mbe_model *m, const float *d_feat, const float *d_target, int32_t n, int32_t epochs,
+                    int32_t batch, float lr, uint64_t seed, void *stream, float *final_loss);
+
 /* ---------------------------------------------------------------- options */
 
 typedef struct {
@@ -111,7 +159,9 @@ typedef struct {
     int32_t blocks_per_sm;    /* resident blocks per SM for the persistent launch; 0 = auto */
     int32_t bitset_max_words; /* widest root-local bitset row, in 64-bit words (1..32); 0 = 32 */
     int32_t steal;            /* 1 = busy workers split their shallowest frame for idle ones (Sec. III-C) */
-    int32_t schedule;         /* 0 = static execution order (descending degree), 1 = learned (model) */
+    int32_t schedule;         /* 0 = static execution order (descending degree); 1 = learned: roots by
+                                 descending predicted cost, predicted-heavy roots split into up to 32
+                                 tasks; 2 = learned order without splitting (needs `model`) */
     int32_t emit;             /* 0 = count + hash only, 1 = also write the bicliques */
     int32_t watchdog_ms;      /* bound on any device wait; 0 = 60000 */
     int32_t root_begin;       /* shard of the execution order: positions [root_begin, root_end) */

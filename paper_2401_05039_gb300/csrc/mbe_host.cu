@@ -10,8 +10,11 @@
 
 #include "../../include/mbe.h"
 #include "mbe_internal.h"
+#include "mbe_learn.h"
 #include "mbe_prep.h"
 #include "mbe_runtime.h"
+
+#include <cmath>
 
 struct mbe_graph {
     int device = 0;
@@ -24,7 +27,21 @@ struct mbe_graph {
     int32_t *order_static = nullptr; // non-isolated U by descending degree
     int32_t *hist = nullptr;         // max(max_deg_u, key range) + 1 entries
     int32_t hist_len = 0;
+    // learned schedule (allocated on first use)
+    float *feat = nullptr;           // [nU][8] root features
+    float *pred = nullptr;           // [nU] predicted log cost
+    int32_t *key = nullptr;          // [nU] order keys
+    int32_t *order_l = nullptr;      // [nU] learned order
+    int32_t *task_root = nullptr;    // [nU + 32 * kSplitHead] tasks of the learned schedule
+    int32_t *task_split = nullptr;
+    int32_t *bad = nullptr;
 };
+
+namespace mbe {
+constexpr int kSplitHead = 1024;  // predicted-heaviest roots considered for splitting
+constexpr int kMaxParts = 32;     // most tasks one root is split into
+constexpr int kMaxKey = 16383;    // order keys: predicted log cost in steps of 1/256
+} // namespace mbe
 
 namespace mbe {
 
@@ -227,6 +244,7 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         a.key_shift = key_bits_for(std::max<int32_t>(in.max_nU, 2));
         a.task_root = in.task_root;
         a.task_graph = in.task_graph;
+        a.task_split = in.task_split;
         a.n_tasks = in.n_tasks;
         a.arena = ws.arena;
         a.arena_bytes = ws.arena_bytes;
@@ -304,6 +322,142 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
     return MBE_ERR_ARENA_FULL;
 }
 
+// Root features of g into d_feat (and d_raw), using the shared workspace's
+// stamp arrays; core numbers are computed on the way.
+int root_features(mbe_graph *g, float *d_feat, int32_t *d_raw, cudaStream_t s)
+{
+    if (g->nU == 0) return MBE_OK;
+    Workspace &ws = device_workspace();
+    mbe_options o;
+    mbe_default_options(&o);
+    int st = ensure_workspace(ws, g->nc_max, g->urow_max, g->frame_max, g->nU, choose_shape(o), 0, 2);
+    if (st != MBE_OK) return st;
+    const int n = g->nU + g->nV;
+    int32_t *tmp = nullptr, *raw = nullptr;
+    if (cudaMalloc(&tmp, sizeof(int32_t) * (3 * (size_t)n + 1 + (size_t)g->max_deg_u + 1)) != cudaSuccess ||
+        (!d_raw && cudaMalloc(&raw, sizeof(int32_t) * 8 * (size_t)g->nU) != cudaSuccess)) {
+        cudaFree(tmp);
+        cudaGetLastError();
+        return MBE_ERR_OOM;
+    }
+    int32_t *deg = tmp, *alive = tmp + n, *core = tmp + 2 * n, *removed = tmp + 3 * n, *larger = removed + 1;
+    cudaError_t e = compute_core_numbers(g->u_off, g->u_adj, g->v_off, g->v_adj, g->nU, g->nV, deg, alive, core,
+                                         removed, s);
+    if (e == cudaSuccess) e = degree_larger(g->u_off, g->nU, g->max_deg_u, larger, s);
+    const int nw = ws.n_warps / 8 * 8;
+    if (e == cudaSuccess)
+        e = compute_root_features(g->u_off, g->u_adj, g->v_off, g->v_adj, g->nU, larger, core, ws.mark, ws.mark_stride,
+                                  nw, d_raw ? d_raw : raw, d_feat, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(tmp);
+    cudaFree(raw);
+    return cuda_status(e);
+}
+
+// The learned execution order: predicted log cost per root, roots by
+// descending prediction (counting sort on quantised keys), and the
+// predicted-heaviest roots split into contiguous shares of their level-1
+// frames (a root predicted above half a worker's fair share of the total is
+// split into up to kMaxParts tasks). Falls back to the static order when a
+// prediction is not finite.
+int learned_schedule(mbe_graph *g, const mbe_model *md, bool presplit, cudaStream_t s, int64_t *n_tasks,
+                     bool *fallback, double *prep_ms)
+{
+    const int nU = g->nU;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    if (!g->feat) {
+        const size_t cap = (size_t)nU + (size_t)kMaxParts * kSplitHead;
+        if (cudaMalloc(&g->feat, sizeof(float) * 8 * (size_t)nU) != cudaSuccess ||
+            cudaMalloc(&g->pred, sizeof(float) * (size_t)nU) != cudaSuccess ||
+            cudaMalloc(&g->key, sizeof(int32_t) * (size_t)nU) != cudaSuccess ||
+            cudaMalloc(&g->order_l, sizeof(int32_t) * (size_t)nU) != cudaSuccess ||
+            cudaMalloc(&g->task_root, sizeof(int32_t) * cap) != cudaSuccess ||
+            cudaMalloc(&g->task_split, sizeof(int32_t) * cap) != cudaSuccess ||
+            cudaMalloc(&g->bad, sizeof(int32_t)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(g->feat);
+            g->feat = nullptr;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return MBE_ERR_OOM;
+        }
+        int st = root_features(g, g->feat, nullptr, s);
+        if (st != MBE_OK) {
+            cudaFree(g->feat);
+            g->feat = nullptr;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return st;
+        }
+    }
+    cudaError_t e = model_predict(md, g->feat, nU, g->pred, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->bad, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = learned_order_keys(g->pred, g->u_off, nU, kMaxKey, g->key, g->bad, s);
+    if (e == cudaSuccess) e = order_by_key_desc(g->key, nU, kMaxKey, g->hist, g->order_l, s);
+    const int64_t n_live = g->n_live;
+    const int head = (int)std::min<int64_t>(n_live, kSplitHead);
+    std::vector<float> pred((size_t)nU);
+    std::vector<int32_t> top((size_t)head);
+    int32_t bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, g->bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pred.data(), g->pred, sizeof(float) * (size_t)nU, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && head > 0)
+        e = cudaMemcpyAsync(top.data(), g->order_l, sizeof(int32_t) * (size_t)head, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_status(e);
+    }
+    *fallback = bad != 0;
+    int64_t nt = 0;
+    if (!*fallback) {
+        std::vector<int32_t> hr, hs;
+        if (presplit) {
+            double total = 0.0; // predicted nodes over the live roots
+            for (int u = 0; u < nU; ++u)
+                if (std::isfinite(pred[u]) && pred[u] > 0.f) total += std::expm1((double)pred[u]);
+            mbe_options o;
+            mbe_default_options(&o);
+            const double share = total / std::max(1, choose_shape(o).warps);
+            for (int k = 0; k < head; ++k) {
+                const int r = top[k];
+                const double pn = std::expm1((double)pred[r]);
+                int parts = 1;
+                if (share > 0 && pn > 0.5 * share) parts = (int)std::min<double>(kMaxParts, std::ceil(pn / (0.5 * share)));
+                for (int p = 0; p < parts; ++p) {
+                    hr.push_back(r);
+                    hs.push_back(parts > 1 ? (parts << 16) | p : 0);
+                }
+            }
+        } else {
+            hr.assign(top.begin(), top.end());
+            hs.assign(top.size(), 0);
+        }
+        nt = (int64_t)hr.size() + (n_live - head);
+        e = cudaMemcpyAsync(g->task_root, hr.data(), sizeof(int32_t) * hr.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(g->task_split, hs.data(), sizeof(int32_t) * hs.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && n_live > head)
+            e = cudaMemcpyAsync(g->task_root + hr.size(), g->order_l + head, sizeof(int32_t) * (size_t)(n_live - head),
+                                cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && n_live > head)
+            e = cudaMemsetAsync(g->task_split + hr.size(), 0, sizeof(int32_t) * (size_t)(n_live - head), s);
+    }
+    cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *prep_ms = ms;
+    *n_tasks = nt;
+    return cuda_status(e);
+}
+
 } // namespace mbe
 
 using namespace mbe;
@@ -345,6 +499,13 @@ int mbe_graph_destroy(mbe_graph *g)
     cudaFree(g->d_desc);
     cudaFree(g->order_static);
     cudaFree(g->hist);
+    cudaFree(g->feat);
+    cudaFree(g->pred);
+    cudaFree(g->key);
+    cudaFree(g->order_l);
+    cudaFree(g->task_root);
+    cudaFree(g->task_split);
+    cudaFree(g->bad);
     delete g;
     return MBE_OK;
 }
@@ -430,7 +591,7 @@ int mbe_graph_create(int32_t nU, int32_t nV, int64_t nE, const int32_t *u_off, c
         }
         g->max_deg_v = hm;
     }
-    g->hist_len = std::max<int32_t>(g->max_deg_u, 4096) + 1;
+    g->hist_len = std::max<int32_t>(g->max_deg_u, kMaxKey) + 1;
     if (cudaMalloc(&g->order_static, sizeof(int32_t) * (size_t)std::max(nU, 1)) != cudaSuccess ||
         cudaMalloc(&g->hist, sizeof(int32_t) * (size_t)g->hist_len) != cudaSuccess) {
         cudaGetLastError();
@@ -456,6 +617,12 @@ int mbe_debug_trace(uint64_t *host, int32_t max_workers)
     int n = std::min(max_workers, g_debug_warps);
     if (cudaMemcpy(host, g_debug, sizeof(uint64_t) * 16 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
     return n;
+}
+
+int mbe_root_features(const mbe_graph *gc, float *d_feat, int32_t *d_raw, void *stream)
+{
+    if (!gc || (gc->nU > 0 && !d_feat)) return MBE_ERR_INVALID_ARG;
+    return root_features(const_cast<mbe_graph *>(gc), d_feat, d_raw, (cudaStream_t)stream);
 }
 
 int mbe_release_workspace(void)
@@ -497,14 +664,29 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     if (g->nU == 0 || g->n_live == 0) return set_status(out, MBE_OK);
 
     const int32_t *order = g->order_static;
+    const int32_t *split = nullptr;
     int64_t n_order = g->n_live;
+    double prep_ms = 0.0;
     if (o.exec_order) {
         if (o.n_exec < 0 || o.n_exec > g->nU) return set_status(out, MBE_ERR_INVALID_ARG);
         order = o.exec_order;
         n_order = o.n_exec;
-    } else if (o.schedule == 1) {
-        return set_status(out, MBE_ERR_UNSUPPORTED);
+    } else if (o.schedule == 1 || o.schedule == 2) {
+        if (!o.model) return set_status(out, MBE_ERR_INVALID_ARG);
+        int64_t n_tasks = 0;
+        bool fallback = false;
+        int st = learned_schedule(g, static_cast<const mbe_model *>(o.model), o.schedule == 1, s, &n_tasks,
+                                  &fallback, &prep_ms);
+        if (st != MBE_OK) return set_status(out, st);
+        if (!fallback) {
+            order = g->task_root;
+            split = g->task_split;
+            n_order = n_tasks;
+        }
+    } else if (o.schedule != 0) {
+        return set_status(out, MBE_ERR_INVALID_ARG);
     }
+    if (split && (o.root_begin > 0 || o.root_end >= 0)) return set_status(out, MBE_ERR_INVALID_ARG);
     int64_t b = std::max<int64_t>(0, o.root_begin);
     int64_t e = o.root_end < 0 ? n_order : std::min<int64_t>(o.root_end, n_order);
     if (b > e) return set_status(out, MBE_ERR_INVALID_ARG);
@@ -519,6 +701,7 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     in.max_nU = g->nU;
     in.task_root = order + b;
     in.task_graph = nullptr;
+    in.task_split = split;
     in.n_tasks = e - b;
     in.nc_max = g->nc_max;
     in.urow_max = g->urow_max;
@@ -527,6 +710,7 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     in.n_owner = g->nU;
     in.per_mode = 1;
     int st = run_search(device_workspace(), in, o, s, out, bicliques);
+    if (out) out->prep_ms = prep_ms;
     return set_status(out, st);
 }
 

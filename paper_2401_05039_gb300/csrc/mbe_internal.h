@@ -25,6 +25,7 @@ struct SearchArgs {
     int32_t key_shift;      // bits for a vertex id in the (count, id) sort key
     const int32_t *task_root;  // [n_tasks] root (graph-local id) in execution order
     const int32_t *task_graph; // [n_tasks] graph of the task, NULL when n_graphs == 1
+    const int32_t *task_split; // [n_tasks] (parts << 16 | part) of a pre-split root, 0 = whole; or NULL
     int64_t n_tasks;
 
     // per-worker workspace

@@ -318,6 +318,18 @@ cudaError_t order_by_degree_desc(const int32_t *u_off, int32_t nU, int32_t max_d
     return cudaGetLastError();
 }
 
+cudaError_t degree_larger(const int32_t *u_off, int32_t nU, int32_t max_deg, int32_t *d_hist, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(d_hist, 0, sizeof(int32_t) * (size_t)(max_deg + 1), s);
+    if (e != cudaSuccess) return e;
+    int blocks = (nU + 255) / 256;
+    if (blocks > 4 * 152) blocks = 4 * 152;
+    if (blocks < 1) blocks = 1;
+    degree_hist_kernel<<<blocks, 256, 0, s>>>(u_off, nU, d_hist);
+    scan_desc_kernel<<<1, 1024, 0, s>>>(d_hist, max_deg + 1);
+    return cudaGetLastError();
+}
+
 cudaError_t order_by_key_desc(const int32_t *d_key, int32_t n, int32_t max_key, int32_t *d_hist, int32_t *d_order,
                               cudaStream_t s)
 {

@@ -32,6 +32,9 @@ cudaError_t root_bounds(const GraphDesc *d_graphs, int32_t n_graphs, int32_t max
 cudaError_t order_by_degree_desc(const int32_t *u_off, int32_t nU, int32_t max_deg, int32_t *d_hist,
                                  int32_t *d_order, cudaStream_t s);
 
+// d_hist[d] = number of non-isolated U vertices with degree > d (max_deg + 1 entries).
+cudaError_t degree_larger(const int32_t *u_off, int32_t nU, int32_t max_deg, int32_t *d_hist, cudaStream_t s);
+
 // d_order receives every u with d_key[u] >= 0, by descending key (keys <= max_key).
 cudaError_t order_by_key_desc(const int32_t *d_key, int32_t n, int32_t max_key, int32_t *d_hist, int32_t *d_order,
                               cudaStream_t s);

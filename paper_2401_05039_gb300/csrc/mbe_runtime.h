@@ -58,6 +58,7 @@ struct RunInput {
     int32_t n_graphs;
     int32_t max_nU;
     const int32_t *task_root, *task_graph;
+    const int32_t *task_split = nullptr;
     int64_t n_tasks;
     int64_t nc_max, urow_max, frame_max;
     unsigned long long *per_owner; // [n_owner][4], zeroed here before every launch

@@ -636,13 +636,16 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 // universe of N2(r), the check against the earlier-ranked candidates, the
 // expansion by the later-ranked ones, and the level-1 frame at the bottom
 // of the stack. Returns true when a frame was pushed.
-__device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r, int graph)
+__device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r, int graph, int part, int parts)
 {
     const int lane = c.lane;
     const uint64_t t_root = tnow(a);
     const int ro = G.u_off[r];
     const int d = G.u_off[r + 1] - ro;
-    c.nodes += 1;
+    // a pre-split root: every part rebuilds the root node, part 0 alone
+    // counts it, and part p pops its own contiguous share of P'
+    const bool first = part == 0;
+    if (first) c.nodes += 1;
     if (d == 0) return false;
     const int W = (d + 63) >> 6;
     if (W > a.max_words) {
@@ -724,7 +727,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     // reset the marks for the next root
     for (int k = lane; k < nc; k += 32) mark[S.ugid[k]] = -1;
     __syncwarp();
-    c.bytes += 4ULL * ((uint64_t)d + pairs_total);
+    if (first) c.bytes += 4ULL * ((uint64_t)d + pairs_total);
     if (c.abort) return false;
 
     // L' = N(r): all d bits (lane w holds word w)
@@ -776,11 +779,13 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     uint64_t ls = 0;
     for (int j = lane; j < d; j += 32) ls += key_v(G.u_adj[ro + j]);
     ls = warp_sum64(ls);
-    c.cnt += 1;
-    c.hash += splitmix(Rs + ls);
+    if (first) {
+        c.cnt += 1;
+        c.hash += splitmix(Rs + ls);
+    }
 
     prepare_masks(c, Lw, W);
-    if (a.emit) {
+    if (a.emit && first) {
         // L' ids are N(r) itself
         int nR = 1 + nfull;
         int64_t need = 2 + nR + d;
@@ -837,8 +842,8 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         h.W = W;
         h.nQ = qn;
         h.nP = pn;
-        h.i = 0;
-        h.end = pn;
+        h.i = (int32_t)(((int64_t)pn * part) / parts);
+        h.end = (int32_t)(((int64_t)pn * (part + 1)) / parts);
         h.root = r;
         h.graph = graph;
         h.Rsum = Rs;
@@ -1118,11 +1123,13 @@ __global__ void search_kernel(SearchArgs a)
             idle = false;
             int g = a.task_graph ? a.task_graph[t] : 0;
             int r = a.task_root[t];
+            int sp = a.task_split ? a.task_split[t] : 0;
+            int parts = sp ? (sp >> 16) : 1, part = sp ? (sp & 0xffff) : 0;
             GView G = gview(a, g);
             trace(a, c, 1, r);
             backoff = 64;
             uint64_t t_busy = tnow(a);
-            bool pushed = process_root(a, c, G, r, g);
+            bool pushed = process_root(a, c, G, r, g, part, parts);
             c.depth = pushed ? 1 : 0;
             if (pushed && !c.abort) run_stack(a, c, c.arena);
             if (c.lane == 0) {

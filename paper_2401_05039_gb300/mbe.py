@@ -79,6 +79,15 @@ _SIGNATURES = {
     "mbe_enumerate_noalloc": ([_I32, _I32, _I64, _P, _P, _P, _P, _P, ctypes.POINTER(Result)], _I32),
     "mbe_copy_bandwidth": ([_I64, _I32, _P, ctypes.POINTER(ctypes.c_double)], _I32),
     "mbe_batch_class": ([_I32, _I32, _I64], _I32),
+    "mbe_model_create": ([ctypes.c_uint64, ctypes.POINTER(_P)], _I32),
+    "mbe_model_destroy": ([_P], _I32),
+    "mbe_model_set_params": ([_P, _P], _I32),
+    "mbe_model_get_params": ([_P, _P], _I32),
+    "mbe_root_features": ([_P, _P, _P, _P], _I32),
+    "mbe_model_predict": ([_P, _P, _I32, _P, _P], _I32),
+    "mbe_model_loss_grad": ([_P, _P, _P, _I32, _P, ctypes.POINTER(ctypes.c_float), _P], _I32),
+    "mbe_model_train": ([_P, _P, _P, _I32, _I32, _I32, ctypes.c_float, ctypes.c_uint64, _P,
+                         ctypes.POINTER(ctypes.c_float)], _I32),
     "mbe_autotune_batch": ([_I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I32, _P, _P], _I32),
     "mbe_enumerate_batch": ([_I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Options), _P, _P,
                              ctypes.POINTER(Result)], _I32),
@@ -138,6 +147,8 @@ def options(**kw) -> Options:
     for k, v in kw.items():
         if k == "class_params" and v is not None and not isinstance(v, int):
             v = ctypes.cast(v, ctypes.c_void_p).value
+        elif k == "model" and isinstance(v, Model):
+            v = v.handle
         elif k in ("per_root", "exec_order", "model"):
             v = _ptr(v) if not isinstance(v, (int, type(None))) else v
         setattr(o, k, v)
@@ -179,6 +190,22 @@ class Graph:
         if check:
             _check(st, "mbe_enumerate")
         return r
+
+    def features(self, stream=None, raw=False):
+        """mbe_root_features: float32 [nU, 8] CUDA tensor (and the raw int32 values with raw=True)."""
+        import torch
+        f = torch.zeros((self.nU, 8), dtype=torch.float32, device="cuda")
+        r = torch.zeros((self.nU, 8), dtype=torch.int32, device="cuda") if raw else None
+        _check(load().mbe_root_features(self._h, f.data_ptr(), r.data_ptr() if raw else None,
+                                        _stream_handle(stream)), "mbe_root_features")
+        return (f, r) if raw else f
+
+    def per_root(self, stream=None, **kw):
+        """(Result, uint64 numpy [nU, 4]) with the per-root (count, hash, nodes, bytes)."""
+        import torch
+        buf = torch.zeros((self.nU, 4), dtype=torch.int64, device="cuda")
+        r = self.enumerate(stream=stream, per_root=buf, **kw)
+        return r, buf.cpu().numpy().view(np.uint64)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -244,6 +271,83 @@ def enumerate_noalloc(nU, nV, u_off, u_adj, v_off, v_adj, stream=None, check=Tru
     if check:
         _check(st, "mbe_enumerate_noalloc")
     return r
+
+
+class Model:
+    """The cost network (mbe_model_*): FP32 master weights, FP16 copy, trained on the GPU."""
+
+    N_PARAMS = 4801
+
+    def __init__(self, seed: int = 0):
+        h = _P()
+        _check(load().mbe_model_create(ctypes.c_uint64(seed), ctypes.byref(h)), "mbe_model_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.N_PARAMS
+        _check(load().mbe_model_set_params(self._h, p.ctypes.data), "mbe_model_set_params")
+
+    def get_params(self):
+        p = np.zeros(self.N_PARAMS, dtype=np.float32)
+        _check(load().mbe_model_get_params(self._h, p.ctypes.data), "mbe_model_get_params")
+        return p
+
+    def predict(self, feat, stream=None):
+        import torch
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device="cuda")
+        _check(load().mbe_model_predict(self._h, feat.data_ptr(), int(feat.shape[0]), out.data_ptr(),
+                                        _stream_handle(stream)), "mbe_model_predict")
+        return out
+
+    def loss_grad(self, feat, target, stream=None):
+        g = np.zeros(self.N_PARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(load().mbe_model_loss_grad(self._h, feat.data_ptr(), target.data_ptr(), int(feat.shape[0]),
+                                          g.ctypes.data, ctypes.byref(loss), _stream_handle(stream)),
+               "mbe_model_loss_grad")
+        return float(loss.value), g
+
+    def train(self, feat, target, epochs=30, batch=512, lr=3e-3, seed=0, stream=None):
+        loss = ctypes.c_float()
+        _check(load().mbe_model_train(self._h, feat.data_ptr(), target.data_ptr(), int(feat.shape[0]), int(epochs),
+                                      int(batch), ctypes.c_float(lr), ctypes.c_uint64(seed), _stream_handle(stream),
+                                      ctypes.byref(loss)), "mbe_model_train")
+        return float(loss.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mbe_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def training_set(graphs, stream=None):
+    """Features and log1p(subtree nodes) of every non-isolated root of each graph (CUDA tensors).
+
+    The labels are the per-root node counts logged by a plain enumeration of
+    the graph; isolated roots are left out.
+    """
+    import torch
+    feats, targets = [], []
+    for g in graphs:
+        G = Graph.from_synth(g, stream=stream)
+        _, pr = G.per_root(stream=stream)
+        f = G.features(stream=stream)
+        live = torch.from_numpy(np.diff(g.u_off) > 0).cuda()
+        feats.append(f[live])
+        targets.append(torch.log1p(torch.from_numpy(pr[:, 2].astype(np.float64)).cuda()[live]).float())
+        G.close()
+    return torch.cat(feats).contiguous(), torch.cat(targets).contiguous()
 
 
 def release_workspace():
