@@ -193,6 +193,77 @@ def run_reference(args):
     return 0
 
 
+def measure_batched(m, torch):
+    """Batched vs one-call-per-graph on the batch graphs of edge density below 10% (classes 0, 2, 4, 6)."""
+    import synth
+    gs = [synth.batch_graph(3 + i) for i in range(4096)]
+    sel = [g for g in gs if g.nE < 0.1 * g.nU * g.nV]
+    b = synth.pack(sel)
+    m.enumerate_batch(b)  # warm-up (sizes the workspace)
+    per, tot = m.enumerate_batch(b)
+    table = m.autotune_batch(b, sample_per_class=64)
+    per_t, tot_t = m.enumerate_batch(b, class_params=table)
+    assert tot_t.count == tot.count and tot_t.hash == tot.hash
+    # the plain form: one mbe_enumerate per graph (graph resident, device time only)
+    handles = [m.Graph.from_synth(g) for g in sel]
+    handles[0].enumerate()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    c = 0
+    for G in handles:
+        c += int(G.enumerate().count)
+    ev1.record()
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1)
+    for G in handles:
+        G.close()
+    assert c == tot.count
+    n = len(sel)
+    best = min(tot.device_ms, tot_t.device_ms)
+    return {"workload": f"batch4096 graphs with edge density < 0.1 ({n} graphs, {tot.count} bicliques)",
+            "batched_ms_per_graph": best / n, "batched_bicliques_per_s": tot.count / (best * 1e-3),
+            "batched_default_ms": tot.device_ms, "batched_autotuned_ms": tot_t.device_ms,
+            "plain_ms_per_graph": plain_ms / n, "plain_bicliques_per_s": c / (plain_ms * 1e-3),
+            "speedup_batched_over_plain": plain_ms / best}
+
+
+def measure_learned(m, torch):
+    """Static vs learned schedule on the 200k Chung-Lu workload; the model is trained on other graphs."""
+    import synth
+    train = [synth.chung_lu(20000, 50000, 200000, 2.1, 2.3, 2000, 100 + k) for k in range(2)] + \
+            [synth.planted(5000, 5000, 0.01, 60, (15, 25), (20, 40), 0.3, 200 + k) for k in range(2)]
+    t0 = time.time()
+    feat, target = m.training_set(train)
+    model = m.Model(11)
+    loss = model.train(feat, target, epochs=30, batch=512, lr=3e-3, seed=5)
+    train_s = time.time() - t0
+    g = synth.workload("chunglu200k")
+    G = m.Graph.from_synth(g)
+    G.enumerate(schedule=1, model=model)  # warm-up: sizes the workspace, caches the features
+    rs, pr = G.per_root()
+    rl = G.enumerate(schedule=1, model=model)
+    ro = G.enumerate(schedule=2, model=model)
+    assert (rl.count, rl.hash, rl.nodes) == (rs.count, rs.hash, rs.nodes) == (ro.count, ro.hash, ro.nodes)
+    pred = model.predict(G.features()).cpu().numpy()
+    live = np.nonzero(np.diff(g.u_off) > 0)[0]
+    from scipy.stats import spearmanr
+    rho = float(spearmanr(pred[live], np.log1p(pr[live, 2].astype(np.float64))).correlation)
+    mae = float(np.mean(np.abs(pred[live] - np.log1p(pr[live, 2].astype(np.float64)))))
+    G.close()
+    model.close()
+    return {"workload": "chunglu200k (200,000 x 1,000,000, 5,000,000 edges, exponents 2.0/2.2, cap 400, seed 4)",
+            "count": int(rs.count), "static_ms": rs.device_ms, "learned_ms": rl.device_ms + rl.prep_ms,
+            "learned_search_ms": rl.device_ms, "learned_prep_ms": rl.prep_ms,
+            "learned_order_only_ms": ro.device_ms + ro.prep_ms,
+            "static_bicliques_per_s": rs.count / (rs.device_ms * 1e-3),
+            "learned_bicliques_per_s": rl.count / ((rl.device_ms + rl.prep_ms) * 1e-3),
+            "speedup_learned_over_static": rs.device_ms / (rl.device_ms + rl.prep_ms),
+            "model": {"train_graphs": "2 Chung-Lu 20k-shaped (seeds 100, 101) + 2 planted 5k-shaped (seeds 200, 201)",
+                      "train_rows": int(feat.shape[0]), "final_loss": loss, "train_seconds": train_s,
+                      "spearman_pred_vs_measured_nodes": rho, "mae_log1p_nodes": mae}}
+
+
 def run_mbe(args):
     import torch
     import synth
@@ -275,6 +346,9 @@ def run_mbe(args):
     e2e_value = world * e2e_count / (e2e_ms * 1e-3)
 
     l2_gbs = m.copy_bandwidth(32 * 1024 * 1024, iters=10)
+    forms = None
+    if rank == 0 and world == 1 and not args.no_forms:
+        forms = {"batched": measure_batched(m, torch), "learned": measure_learned(m, torch)}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_oracle_sample(g, args.cpu_seconds)
@@ -296,6 +370,7 @@ def run_mbe(args):
                     "steps": e2e_steps, "ms_per_step": e2e_ms / e2e_steps},
             "clocks": clk.summary(),
             "gpu_launches": args.steps,
+            "forms": forms,
         }
         print(json.dumps(line), flush=True)
     G.close()
@@ -312,6 +387,7 @@ def main():
     ap.add_argument("--impl", default="mbe", choices=["mbe", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and learned-schedule forms")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
