@@ -49,7 +49,9 @@ typedef enum {
                                   required sizes are reported in the buffer's n_*_written fields */
     MBE_ERR_TIMEOUT = 6,       /* a device wait exceeded options.watchdog_ms; the kernel stopped cleanly */
     MBE_ERR_CUDA = 7,          /* a CUDA runtime call failed (no device, launch failure, ...) */
-    MBE_ERR_UNSUPPORTED = 8    /* input outside the limits stated at the entry point */
+    MBE_ERR_UNSUPPORTED = 8,   /* input outside the limits stated at the entry point */
+    MBE_ERR_INTERNAL = 9       /* an internal consistency check of the search failed; the launch stopped
+                                  before the access it guards */
 } mbe_status;
 
 /* Human-readable name of a status code (static storage, never NULL). */
@@ -85,8 +87,10 @@ int mbe_graph_info(const mbe_graph *g, int32_t *nU, int32_t *nV, int64_t *nE, in
  * MBE_DEBUG_TRACE set, every search launch keeps a progress record per
  * worker: [0] phase, [1] argument, [2] nodes, [3] depth, [4] donations,
  * [5] steals, [6] elapsed ns, [8..13] ns in root setup, node scans, child
- * builds, frame copies, -, tasks; [14] root tasks, [15] stolen tasks. This
- * copies up to max_workers of them (16 uint64 each) to `host` and
+ * builds, frame copies, sorting, tasks; [14] root tasks, [15] stolen tasks,
+ * [16..21] child builds: sum of |Q'|, sum of |P'|, builds, sum of |L'|, sum
+ * of parent row words, sum of parent candidates. This copies up to
+ * max_workers of them (24 uint64 each) to `host` and
  * returns how many were copied. MBE_DEADLINE_MS bounds any single launch
  * (default 30 minutes); a launch past it stops with MBE_ERR_TIMEOUT.
  */

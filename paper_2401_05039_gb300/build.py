@@ -34,8 +34,15 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Build libmbe.so if any source changed; returns its path."""
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, out: str = None,
+          defines=()) -> str:
+    """Build libmbe.so if any source changed; returns its path.
+
+    ``out`` and ``defines`` build a variant elsewhere (e.g. another register budget)."""
+    global BUILD, LIB
+    if out is not None:
+        BUILD, LIB = os.path.dirname(out), out
+        force = True
     os.makedirs(BUILD, exist_ok=True)
     deps = _deps()
     if not force and not _stale(LIB, deps):
@@ -45,7 +52,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *FLAGS, *extra, *[f"-D{d}" for d in defines], "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -106,13 +106,13 @@ unsigned long long *debug_buffer(int n_warps)
         cudaFree(g_debug);
         g_debug = nullptr;
         g_debug_warps = 0;
-        if (cudaMalloc(&g_debug, sizeof(unsigned long long) * 16 * (size_t)n_warps) != cudaSuccess) {
+        if (cudaMalloc(&g_debug, sizeof(unsigned long long) * 24 * (size_t)n_warps) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
         g_debug_warps = n_warps;
     }
-    cudaMemset(g_debug, 0, sizeof(unsigned long long) * 16 * (size_t)n_warps);
+    cudaMemset(g_debug, 0, sizeof(unsigned long long) * 24 * (size_t)n_warps);
     return g_debug;
 }
 
@@ -153,7 +153,7 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
 {
     const int64_t ncap = std::max<int64_t>(nc_max, 32);
     const int64_t urow = round_up(std::max<int64_t>(urow_max, 256), 256);
-    const int64_t scratch = round_up(5 * round_up(4 * ncap, 16) + 16 * ncap + urow + 256, 256);
+    const int64_t scratch = scratch_layout_bytes(ncap, urow);
     int64_t stack = stack_bytes_req > 0 ? stack_bytes_req : (int64_t)stack_factor * frame_max + (256 << 10);
     stack = round_up(stack, 256);
     const int64_t arena = stack + scratch;
@@ -476,6 +476,7 @@ const char *mbe_status_string(int status)
     case MBE_ERR_TIMEOUT: return "MBE_ERR_TIMEOUT";
     case MBE_ERR_CUDA: return "MBE_ERR_CUDA";
     case MBE_ERR_UNSUPPORTED: return "MBE_ERR_UNSUPPORTED";
+    case MBE_ERR_INTERNAL: return "MBE_ERR_INTERNAL";
     default: return "MBE_ERR_UNKNOWN";
     }
 }
@@ -615,7 +616,7 @@ int mbe_debug_trace(uint64_t *host, int32_t max_workers)
 {
     if (!g_debug || !host) return 0;
     int n = std::min(max_workers, g_debug_warps);
-    if (cudaMemcpy(host, g_debug, sizeof(uint64_t) * 16 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    if (cudaMemcpy(host, g_debug, sizeof(uint64_t) * 24 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
     return n;
 }
 

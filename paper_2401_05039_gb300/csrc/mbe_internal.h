@@ -74,7 +74,35 @@ enum : int32_t {
     kErrArena = MBE_ERR_ARENA_FULL,
     kErrTimeout = MBE_ERR_TIMEOUT,
     kErrUnsupported = MBE_ERR_UNSUPPORTED,
+    kErrInternal = MBE_ERR_INTERNAL,
 };
+
+// Bytes of a worker's scratch region (top of its arena) for lists of
+// `ncap` candidates and root-universe rows of `urow_bytes`; the kernel lays
+// the region out in the same order: five int32 lists, two uint64 key lists,
+// the L' position list (2048 entries), the Q' mask, its word offsets and its
+// compress masks (one entry per 64 candidates), then the universe rows.
+inline int64_t scratch_layout_bytes(int64_t ncap, int64_t urow_bytes)
+{
+    auto p16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+    const int64_t qw = (ncap + 63) / 64 + 1;
+    const int64_t b =
+        5 * p16(4 * ncap) + 2 * p16(8 * ncap) + p16(4 * 2048) + p16(8 * qw) + p16(4 * qw) + p16(56 * qw) + urow_bytes + 256;
+    return (b + 255) / 256 * 256;
+}
+
+// Upper bound of the level-1 frame of a root of degree d with at most nc
+// candidates: header, L ids, Q columns (d x ceil(nc/64) words), P ids,
+// P rows (32-row tiles of ceil(d/64) words), R ids.
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int64_t level1_frame_bound(int64_t d, int64_t nc)
+{
+    const int64_t W = (d + 63) / 64;
+    return 64 + (4 * d + 15) / 16 * 16 + (8 * d * ((nc + 63) / 64) + 15) / 16 * 16 + (4 * nc + 15) / 16 * 16 +
+           256 * W * ((nc + 31) / 32) + (4 * (nc + 1) + 15) / 16 * 16;
+}
 
 // Launch the persistent search kernel on stream (grid = blocks, block = threads).
 cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);

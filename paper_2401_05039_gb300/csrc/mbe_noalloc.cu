@@ -108,7 +108,7 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     used += align256(sizeof(int32_t) * (size_t)(max_deg + 1));
     const int64_t ncap = std::max<int64_t>(nc_max, 32);
     const int64_t urow = (int64_t)align256((size_t)std::max<int64_t>(urow_max, 256));
-    const int64_t scratch = (int64_t)align256((size_t)(5 * ((4 * ncap + 15) / 16 * 16) + 16 * ncap + urow + 256));
+    const int64_t scratch = scratch_layout_bytes(ncap, urow);
     const int64_t slot = (int64_t)align256((size_t)std::max<int64_t>(frame_max, 4096));
     const int64_t mark_stride = (nU + 63) / 64 * 64;
     const int64_t min_stack = (int64_t)align256((size_t)(2 * frame_max + (256 << 10)));

@@ -88,7 +88,7 @@ __global__ void root_bounds_kernel(const GraphDesc *graphs, int32_t n_graphs, co
         long long W = (d + 63) / 64;
         long long tiles = (nc + 31) / 32;
         unsigned long long urow = 256ULL * W * tiles;
-        unsigned long long frame = 64 + ((4ULL * d + 15) & ~15ULL) + 2 * ((4ULL * nc + 15) & ~15ULL) + urow + 16;
+        unsigned long long frame = (unsigned long long)level1_frame_bound(d, nc);
         m_nc = max(m_nc, (unsigned long long)nc);
         m_urow = max(m_urow, urow);
         m_frame = max(m_frame, frame);
@@ -232,7 +232,7 @@ __global__ void graph_bounds_kernel(const GraphDesc *graphs, const int32_t *u_of
         long long nc = s < (long long)G.nU - 1 ? s : (long long)G.nU - 1;
         long long W = (d + 63) / 64, tiles = (nc + 31) / 32;
         unsigned long long urow = 256ULL * W * tiles;
-        unsigned long long frame = 64 + ((4ULL * d + 15) & ~15ULL) + 2 * ((4ULL * nc + 15) & ~15ULL) + urow + 16;
+        unsigned long long frame = (unsigned long long)level1_frame_bound(d, nc);
         m_nc = max(m_nc, (unsigned long long)nc);
         m_urow = max(m_urow, urow);
         m_frame = max(m_frame, frame);

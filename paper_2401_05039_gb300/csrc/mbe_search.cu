@@ -12,16 +12,22 @@
 //
 // Data layout (replaces the paper's compact arrays and lookup tables,
 // Section III-B and III-D): a root builds its local universe, the rows
-// bit(N(u) n N(r)) over the positions of N(r) for every u in N2(r). Every
-// frame stores its candidates' rows packed to its own level set L (bit j
-// of a row = adjacency to the j-th vertex of L), 64-bit words, in tiles of
-// 32 rows stored word-major so that lane k of a warp reads row 32t+k with
-// coalesced loads. A child frame re-packs the rows of its candidates to L'
-// with the bit compression of mbe_bits.h, so deep frames are mostly one
-// word per row. Maximality checking and maximal expansion (Algorithm 1,
-// steps 3 and 4) are AND + popcount over these rows, one candidate per
-// lane, with a warp ballot for the early rejection and prefix sums (ballot
-// + popc) for the compaction of Q' and P'.
+// bit(N(u) n N(r)) over the positions of N(r) for every u in N2(r). A
+// frame with level set L (m vertices) keeps
+//  - its candidates P as rows packed to L (bit j = adjacency to the j-th
+//    vertex of L), 64-bit words, in tiles of 32 rows stored word-major so
+//    lane k of a warp reads row 32t+k with coalesced loads;
+//  - its inherited maximality-check set Q transposed, as m columns: column
+//    j is a bitset over Q of the members adjacent to the j-th vertex of L.
+//    "Some q in Q has N(q) >= L'" is then an AND of the |L'| columns of L'
+//    (the paper's reverse scanning, Section III-D: iterate over L' instead
+//    of Q), 64 candidates per word, stopping as soon as it is empty, and Q'
+//    is the OR of the same columns.
+// A child frame re-packs P' rows to L' and compresses the chosen Q columns
+// by the Q' mask (bit compression of mbe_bits.h), so deep frames stay small.
+// Expansion (Algorithm 1, step 4) and the check against the P entries
+// popped earlier are AND + popcount over P rows, one candidate per lane,
+// with warp ballots for rejection and prefix sums for compaction.
 //
 // Frames live on a per-warp stack in device memory (an arena slice); the
 // stack top is L1/L2 resident. P' is ordered by (|N(v) n L'|, id) once when
@@ -36,7 +42,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
 // active-word masks lw[32] u64, active-word indices aw[32] i32
-constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32;
+constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32 + 34 * 2;
 constexpr int kTiles = 4; // 32-row tiles whose loads a lane keeps in flight together
 
 __device__ __forceinline__ unsigned lanemask_lt()
@@ -63,17 +69,17 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v)
 __device__ __forceinline__ int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
 
 struct __align__(16) FrameHdr {
-    int32_t m;       // |L|: bits per row
-    int32_t W;       // 64-bit words per row
-    int32_t nQ;      // inherited maximality-check candidates (positions 0..nQ-1)
-    int32_t nP;      // candidates to pop, sorted (positions nQ..nQ+nP-1)
+    int32_t m;       // |L|: bits per P row and number of Q columns
+    int32_t W;       // 64-bit words per P row
+    int32_t nQ;      // inherited maximality-check candidates (bits per Q column)
+    int32_t nP;      // candidates to pop, sorted by (count, id)
     int32_t i;       // next P position to pop
     int32_t end;     // one past the last P position this worker pops
     int32_t root;    // top-level candidate of this subtree (graph-local id)
     int32_t graph;   // graph of the subtree
     uint64_t Rsum;   // sum of key_u over R
     int32_t nR;      // |R| stored in the frame (emit mode), else 0
-    int32_t depth;
+    int32_t QW;      // 64-bit words per Q column
     int64_t bytes;   // size of the frame
     int64_t parent;  // offset of the parent frame from the arena base, -1 at the bottom
 };
@@ -82,28 +88,32 @@ static_assert(sizeof(FrameHdr) == 64, "frame header is 64 bytes");
 struct Frame {
     FrameHdr *h;
     int32_t *Lid;    // [m] vertex ids of L (V side)
-    int32_t *gid;    // [n] candidate ids (U side)
-    uint64_t *rows;  // [ceil(n/32)][W][32]
+    uint64_t *Q;     // [m][QW] Q columns
+    int32_t *gid;    // [nP] P candidate ids (U side)
+    uint64_t *rows;  // [ceil(nP/32)][W][32] P rows
     int32_t *R;      // [nR]
 };
 
-__device__ __forceinline__ int64_t frame_bytes(int m, int n, int W, int nR)
+__device__ __forceinline__ int64_t frame_bytes(int m, int QW, int nP, int W, int nR)
 {
-    int64_t tiles = (n + 31) >> 5;
-    return 64 + pad16(4LL * m) + pad16(4LL * n) + 256LL * W * tiles + pad16(4LL * nR);
+    int64_t tiles = (nP + 31) >> 5;
+    // every section is a multiple of 16 bytes: frames are copied with 16-byte accesses
+    return 64 + pad16(4LL * m) + pad16(8LL * m * QW) + pad16(4LL * nP) + 256LL * W * tiles + pad16(4LL * nR);
 }
 
-__device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W)
+__device__ __forceinline__ Frame frame_at(char *p, int m, int QW, int nP, int W)
 {
     Frame f;
     f.h = reinterpret_cast<FrameHdr *>(p);
     char *q = p + 64;
     f.Lid = reinterpret_cast<int32_t *>(q);
     q += pad16(4LL * m);
+    f.Q = reinterpret_cast<uint64_t *>(q);
+    q += pad16(8LL * m * QW);
     f.gid = reinterpret_cast<int32_t *>(q);
-    q += pad16(4LL * n);
+    q += pad16(4LL * nP);
     f.rows = reinterpret_cast<uint64_t *>(q);
-    q += 256LL * W * ((n + 31) >> 5);
+    q += 256LL * W * ((nP + 31) >> 5);
     f.R = reinterpret_cast<int32_t *>(q);
     return f;
 }
@@ -111,7 +121,7 @@ __device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W)
 __device__ __forceinline__ Frame frame_of(char *p)
 {
     const FrameHdr *h = reinterpret_cast<const FrameHdr *>(p);
-    return frame_at(p, h->m, h->nQ + h->nP, h->W);
+    return frame_at(p, h->m, h->QW, h->nP, h->W);
 }
 
 __device__ __forceinline__ int64_t row_word(int k, int w, int W)
@@ -146,7 +156,11 @@ struct Scratch {
     uint64_t *pkey2;
     int32_t *rtmp;  // ids that join R' (emit)
     int32_t *ugid;  // root universe: candidate ids
-    uint64_t *urows;// root universe rows
+    int32_t *jlist; // positions (in L) of the bits of L'
+    uint64_t *mq;   // Q' mask over the inherited Q (one word per 64 candidates)
+    int32_t *offq;  // exclusive prefix of popcount(mq) per word
+    uint64_t *cmq;  // compress stage masks of every mq word (6 per word)
+    uint64_t *urows;// root universe rows; child rows of earlier P entries at other nodes
     int64_t ncap;   // capacity of the lists
     int64_t urow_words;
 };
@@ -163,8 +177,9 @@ struct Ctx {
     uint64_t *cm;     // shared [32][7]: per word mask + 6 compress stage masks
     uint64_t *lw;     // shared [32]: the nonzero words of L', in order
     int32_t *aw;      // shared [32]: their word indices
+    uint64_t *sbuf;   // shared [34]: staging of compressed Q column words
     int na;           // number of nonzero words of L'
-    uint64_t tm[8];   // debug: ns in root setup, scans, child build, copies, idle, busy
+    uint64_t tm[16];  // debug: ns in root setup, scans, child build, copies, sort, busy; counters
     uint64_t cnt, hash, nodes, bytes; // current task (uniform across lanes)
     uint64_t t_cnt, t_hash, t_nodes, t_bytes, t_don, t_steal;
     int since_check;
@@ -177,7 +192,7 @@ struct Ctx {
 __device__ __forceinline__ void trace(const SearchArgs &a, const Ctx &c, int phase, long long arg)
 {
     if (a.debug && c.lane == 0) {
-        unsigned long long *d = a.debug + 16LL * c.wid;
+        unsigned long long *d = a.debug + 24LL * c.wid;
         d[0] = (unsigned long long)phase;
         d[1] = (unsigned long long)arg;
         d[2] = c.t_nodes + c.nodes;
@@ -185,7 +200,7 @@ __device__ __forceinline__ void trace(const SearchArgs &a, const Ctx &c, int pha
         d[4] = c.t_don;
         d[5] = c.t_steal;
         d[6] = globaltimer() - c.t_start;
-        for (int q = 0; q < 8; ++q) d[8 + q] = c.tm[q];
+        for (int q = 0; q < 16; ++q) d[8 + q] = c.tm[q];
     }
 }
 
@@ -362,7 +377,7 @@ __device__ __forceinline__ void count_tiles(const Ctx &c, const uint64_t *rows, 
 // ------------------------------------------------------------- child frames
 // Lane w (< W) holds word w of L' in Lw. Publishes per-word compress masks
 // and the bit offset of every word's first selected bit in shared memory.
-__device__ __forceinline__ void prepare_masks(Ctx &c, uint64_t Lw, int W)
+__device__ __forceinline__ void prepare_offsets(Ctx &c, uint64_t Lw, int W)
 {
     int pc = __popcll(Lw);
     int incl = pc;
@@ -371,15 +386,26 @@ __device__ __forceinline__ void prepare_masks(Ctx &c, uint64_t Lw, int W)
         int y = __shfl_up_sync(kFull, incl, o);
         if (c.lane >= o) incl += y;
     }
+    if (c.lane < W) c.off[c.lane] = incl - pc; // bit offset of word w
+    __syncwarp();
+}
+
+__device__ __forceinline__ void prepare_cm(Ctx &c, uint64_t Lw, int W)
+{
     if (c.lane < W) {
         CompressMasks cm = compress_prepare(Lw);
         uint64_t *dst = c.cm + c.lane * 7;
         dst[0] = Lw;
 #pragma unroll
         for (int i = 0; i < 6; ++i) dst[1 + i] = cm.mv[i];
-        c.off[c.lane] = incl - pc; // bit offset of word w
     }
     __syncwarp();
+}
+
+__device__ __forceinline__ void prepare_masks(Ctx &c, uint64_t Lw, int W)
+{
+    prepare_offsets(c, Lw, W);
+    prepare_cm(c, Lw, W);
 }
 
 // Writes the rows of a child frame: row k' is source row src(k') of the
@@ -488,68 +514,273 @@ __device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase,
     compact_ids(c, Lid, Lw, W, o + 2 + nR);
 }
 
+// ---------------------------------------------------------------- Q columns
+// Positions (in L) of the bits of L', ascending (lane w holds word w of L';
+// offsets from prepare_masks).
+__device__ __forceinline__ void bit_positions(Ctx &c, uint64_t Lw, int W, int32_t *dst)
+{
+    if (c.lane < W) {
+        int pos = c.off[c.lane];
+        uint64_t b = Lw;
+        while (b) {
+            int t = __ffsll(b) - 1;
+            b &= b - 1;
+            dst[pos++] = c.lane * 64 + t;
+        }
+    }
+    __syncwarp();
+}
+
+// True when some inherited q has N(q) >= L': the AND of the columns listed
+// in J is nonempty. Four words per lane in flight; a 128-word chunk stops as
+// soon as its running AND is empty.
+__device__ bool q_any_superset(const Ctx &c, const uint64_t *Q, int QW, const int32_t *J, int mp)
+{
+    const int lane = c.lane;
+    for (int w0 = 0; w0 < QW; w0 += 128) {
+        uint64_t acc[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[k] = (w0 + 32 * k + lane < QW) ? ~0ULL : 0ULL;
+        int jreg = 0;
+        for (int t = 0; t < mp; ++t) {
+            if ((t & 31) == 0) jreg = t + lane < mp ? J[t + lane] : 0;
+            const int j = __shfl_sync(kFull, jreg, t & 31);
+            const uint64_t *col = Q + (int64_t)j * QW + w0 + lane;
+            uint64_t x[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) x[k] = (w0 + 32 * k + lane < QW) ? col[32 * k] : 0ULL;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] &= x[k];
+            if ((t & 3) == 3 && !__any_sync(kFull, (acc[0] | acc[1] | acc[2] | acc[3]) != 0)) break;
+        }
+        if (__any_sync(kFull, (acc[0] | acc[1] | acc[2] | acc[3]) != 0)) return true;
+    }
+    return false;
+}
+
+// Q' over the inherited Q: mq = OR of the columns listed in J, offq = its
+// per-word exclusive popcount prefix, cmq = its compress stage masks.
+// Returns |Q'| (inherited part).
+__device__ int q_union_mask(Ctx &c, const uint64_t *Q, int QW, const int32_t *J, int mp)
+{
+    const int lane = c.lane;
+    Scratch &S = c.s;
+    int run = 0;
+    for (int w0 = 0; w0 < QW; w0 += 32) {
+        const int w = w0 + lane;
+        const bool v = w < QW;
+        const uint64_t *base = Q + (v ? w : 0);
+        uint64_t m0 = 0, m1 = 0;
+        int t = 0;
+        for (; t + 2 <= mp; t += 2) {
+            const uint64_t x0 = base[(int64_t)J[t] * QW], x1 = base[(int64_t)J[t + 1] * QW];
+            m0 |= x0;
+            m1 |= x1;
+        }
+        if (t < mp) m0 |= base[(int64_t)J[t] * QW];
+        const uint64_t m = v ? (m0 | m1) : 0ULL;
+        const int pc = __popcll(m);
+        int incl = pc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (v) {
+            S.mq[w] = m;
+            S.offq[w] = run + incl - pc;
+            CompressMasks cm = compress_prepare(m);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) S.cmq[6 * (int64_t)w + i] = cm.mv[i];
+        }
+        run += __shfl_sync(kFull, incl, 31);
+    }
+    __syncwarp();
+    return run;
+}
+
+// Child Q column t = parent column J[t] compressed by mq, for every t < mp:
+// each 32-word chunk of the parent column is compressed lane-wise and
+// assembled in shared memory, then written out; only the first word of a
+// chunk can hold bits of the previous chunk (it is OR-ed). dst is zeroed.
+__device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, const int32_t *J, int mp, uint64_t *dst,
+                                int QWd)
+{
+    const int lane = c.lane;
+    Scratch &S = c.s;
+    if (QW <= 8) {
+        // short columns: one lane per child column, bits appended in registers
+        for (int t = lane; t < mp; t += 32) {
+            const uint64_t *col = Q + (int64_t)J[t] * QW;
+            uint64_t *out = dst + (int64_t)t * QWd;
+            uint64_t cur = 0;
+            int o = 0, b = 0;
+            for (int w = 0; w < QW; ++w) {
+                CompressMasks cm;
+                cm.m = S.mq[w];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) cm.mv[i] = S.cmq[6 * (int64_t)w + i];
+                const int nb = __popcll(cm.m);
+                if (nb == 0) continue;
+                const uint64_t v = compress_apply(col[w], cm);
+                cur |= v << b;
+                if (b + nb >= 64) {
+                    out[o++] = cur;
+                    cur = (b + nb > 64) ? (v >> (64 - b)) : 0;
+                    b = b + nb - 64;
+                } else {
+                    b += nb;
+                }
+            }
+            if (b > 0) out[o] = cur;
+        }
+        __syncwarp();
+        return;
+    }
+    for (int t = 0; t < mp; ++t) {
+        const uint64_t *col = Q + (int64_t)J[t] * QW;
+        uint64_t *out = dst + (int64_t)t * QWd;
+        for (int w0 = 0; w0 < QW; w0 += 32) {
+            const int w = w0 + lane;
+            const bool v = w < QW;
+            uint64_t val = 0;
+            int nb = 0, off = 0;
+            if (v) {
+                CompressMasks cm;
+                cm.m = S.mq[w];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) cm.mv[i] = S.cmq[6 * (int64_t)w + i];
+                val = compress_apply(col[w], cm);
+                nb = __popcll(cm.m);
+                off = S.offq[w];
+            }
+            const int first = __shfl_sync(kFull, off, 0);
+            const int k0 = first >> 6;
+            const int last_lane = min(31, QW - 1 - w0);
+            const int end_bit = __shfl_sync(kFull, off + nb, last_lane);
+            if (end_bit == first) continue;
+            const int k1 = (end_bit - 1) >> 6;
+            for (int q = lane; q <= k1 - k0; q += 32) c.sbuf[q] = 0;
+            __syncwarp();
+            if (nb) {
+                const int rel = off - (k0 << 6);
+                const int kk = rel >> 6, b = rel & 63;
+                atomicOr(reinterpret_cast<unsigned long long *>(&c.sbuf[kk]), (unsigned long long)(val << b));
+                if (b + nb > 64)
+                    atomicOr(reinterpret_cast<unsigned long long *>(&c.sbuf[kk + 1]),
+                             (unsigned long long)(val >> (64 - b)));
+            }
+            __syncwarp();
+            for (int q = lane; q <= k1 - k0; q += 32) out[k0 + q] = q == 0 ? (out[k0] | c.sbuf[0]) : c.sbuf[q];
+            __syncwarp();
+        }
+    }
+}
+
+// Transposes n rows (tile layout, Wr words, row k taken from position
+// pos[k] or k) into ncols column bitsets of QWd words, writing the rows as
+// bits bit0 .. bit0+n-1 of every column (OR into zeroed columns).
+__device__ void rows_to_columns(Ctx &c, const uint64_t *rows, int Wr, const int32_t *pos, int n, int ncols,
+                                uint64_t *cols, int QWd, int bit0)
+{
+    const int lane = c.lane;
+    for (int t0 = 0; t0 < n; t0 += 32) {
+        const int k = t0 + lane;
+        const bool valid = k < n;
+        const int src = valid ? (pos ? pos[k] : k) : 0;
+        const uint64_t *r = rows + row_word(src, 0, Wr);
+        for (int jb = 0; jb < ncols; jb += 32) {
+            const uint64_t x = valid ? r[(jb >> 6) * 32] : 0ULL;
+            const int sh = jb & 63;
+            unsigned mine = 0;
+            const int nq = min(32, ncols - jb);
+            for (int q = 0; q < nq; ++q) {
+                const unsigned bal = __ballot_sync(kFull, (x >> (sh + q)) & 1ULL);
+                if (lane == q) mine = bal;
+            }
+            const int colj = jb + lane;
+            if (colj < ncols && mine) {
+                const int p = bit0 + t0;
+                uint64_t *cw = cols + (int64_t)colj * QWd + (p >> 6);
+                const int b = p & 63;
+                cw[0] |= (uint64_t)mine << b;
+                if (b > 32 && ((uint64_t)mine >> (64 - b)) != 0) cw[1] |= (uint64_t)mine >> (64 - b);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ void zero_words(Ctx &c, uint64_t *p, int64_t n)
+{
+    for (int64_t k = c.lane; k < n; k += 32) p[k] = 0;
+    __syncwarp();
+}
+
 // ------------------------------------------------------------ node (frame)
 // One iteration of Algorithm 1's while loop on the top frame at fp: pop
 // x = P[i], build L' = L n N(x) (= row of x), check maximality against the
-// Q-like positions (inherited Q and the P entries popped earlier), expand
-// R' and collect P' from the later positions, emit, and push the child
-// frame when P' is nonempty. Returns the child's address or NULL.
+// inherited Q (column AND) and the P entries popped earlier (row scan),
+// expand R' and collect P' from the later P entries, emit, and push the
+// child frame when P' is nonempty. Returns the child's address or NULL.
 __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 {
     const int lane = c.lane;
     Frame F = frame_of(fp);
-    const int W = F.h->W, nQ = F.h->nQ, nP = F.h->nP, n = nQ + nP;
+    const int W = F.h->W, nQ = F.h->nQ, QW = F.h->QW, nP = F.h->nP;
     const int i = F.h->i;
-    const int kx = nQ + i;
     __syncwarp(); // every lane has read the header before lane 0 advances the cursor
     if (lane == 0) F.h->i = i + 1;
     c.nodes += 1;
 
     // Step 2: L' = L n N(x) is the row of x (lane w holds word w).
     uint64_t t_scan = tnow(a);
-    uint64_t Lw = lane < W ? F.rows[row_word(kx, lane, W)] : 0ULL;
+    const uint64_t Lw = lane < W ? F.rows[row_word(i, lane, W)] : 0ULL;
     const int mp = __reduce_add_sync(kFull, (unsigned)__popcll(Lw));
     set_active_words(c, Lw);
-
-    // Step 3: maximality check over positions [0, kx).
+    prepare_offsets(c, Lw, W);
     Scratch &S = c.s;
-    int qn = 0;
-    bool rejected = false;
-    const int q_end = (kx + 31) >> 5;
+    bit_positions(c, Lw, W, S.jlist);
+
+    // Step 3: maximality check: the inherited Q (columns), then the P
+    // entries popped before x (rows, positions [0, i)).
+    bool rejected = nQ > 0 && q_any_superset(c, F.Q, QW, S.jlist, mp);
+    int qb = 0;
+    const int q_end = (i + 31) >> 5;
     for (int t0 = 0; t0 < q_end && !rejected; t0 += kTiles) {
         int cnt[kTiles];
         count_tiles<kTiles>(c, F.rows, W, t0, q_end, cnt);
 #pragma unroll
         for (int u = 0; u < kTiles; ++u) {
             const int k = (t0 + u) * 32 + lane;
-            const bool valid = (t0 + u < q_end) && k < kx;
+            const bool valid = (t0 + u < q_end) && k < i;
             if (__ballot_sync(kFull, valid && cnt[u] == mp)) {
                 rejected = true;
                 break;
             }
             const bool part = valid && cnt[u] > 0;
             const unsigned bal = __ballot_sync(kFull, part);
-            if (part) S.qsrc[qn + __popc(bal & lanemask_lt())] = k;
-            qn += __popc(bal);
+            if (part) S.qsrc[qb + __popc(bal & lanemask_lt())] = k;
+            qb += __popc(bal);
         }
     }
-    c.bytes += 8ULL * (uint64_t)W * (uint64_t)(1 + kx + (rejected ? 0 : (n - kx - 1)));
+    c.bytes += 8ULL * (uint64_t)W * (uint64_t)(1 + nQ + i + (rejected ? 0 : (nP - i - 1)));
     if (rejected) {
         if (lane == 0) tadd(a, c, 1, t_scan);
         return nullptr;
     }
 
-    // Step 4: maximal expansion over positions (kx, n).
+    // Step 4: maximal expansion over P positions (i, nP).
     uint64_t rsum = 0;
     int pn = 0, nfull = 0;
-    const int ntiles = (n + 31) >> 5;
-    for (int t0 = (kx + 1) >> 5; t0 < ntiles; t0 += kTiles) {
+    const int ntiles = (nP + 31) >> 5;
+    for (int t0 = (i + 1) >> 5; t0 < ntiles; t0 += kTiles) {
         int cnt[kTiles];
         count_tiles<kTiles>(c, F.rows, W, t0, ntiles, cnt);
 #pragma unroll
         for (int u = 0; u < kTiles; ++u) {
             const int k = (t0 + u) * 32 + lane;
-            const bool valid = (t0 + u < ntiles) && k > kx && k < n;
+            const bool valid = (t0 + u < ntiles) && k > i && k < nP;
             const bool full = valid && cnt[u] == mp;
             const bool part = valid && cnt[u] > 0 && cnt[u] < mp;
             const int g = (full || part) ? F.gid[k] : 0;
@@ -570,39 +801,67 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     }
     if (lane == 0) tadd(a, c, 1, t_scan);
     rsum = warp_sum64(rsum);
-    const int xg = F.gid[kx];
+    const int xg = F.gid[i];
     const uint64_t Rs = F.h->Rsum + key_u(xg) + rsum;
     const uint64_t lsum = sum_keys_v(c, F.Lid, Lw, W);
     c.cnt += 1;
     c.hash += splitmix(Rs + lsum);
 
     uint64_t t_build = tnow(a);
-    if (a.emit || pn > 0) prepare_masks(c, Lw, W);
     if (a.emit) emit_biclique(a, c, F.R, F.h->nR, xg, S.rtmp, nfull, F.Lid, Lw, W, mp);
+    if (pn > 0) prepare_cm(c, Lw, W);
     if (pn == 0) {
         if (lane == 0) tadd(a, c, 2, t_build);
         return nullptr;
     }
 
-    // Child frame: [Q' | P' sorted by (count, id)], rows packed to L'.
+    // Child frame: Q' (inherited members touching L', then the earlier P
+    // entries with 0 < count < |L'|) as columns over L', P' rows sorted by
+    // (count, id), all packed to L'.
     const int Wd = (mp + 63) >> 6;
-    const int nd = qn + pn;
+    const int nq1 = nQ > 0 ? q_union_mask(c, F.Q, QW, S.jlist, mp) : 0;
+    const int nQd = nq1 + qb;
+    const int QWd = (nQd + 63) >> 6;
     const int nRd = a.emit ? F.h->nR + 1 + nfull : 0;
-    const int64_t sz = frame_bytes(mp, nd, Wd, nRd);
+    const int64_t sz = frame_bytes(mp, QWd, pn, Wd, nRd);
     char *cp = fp + F.h->bytes;
-    if (cp + sz > c.limit) {
+    if (((uintptr_t)cp & 15) || (sz & 15)) {
+        if (lane == 0) set_error(a, kErrInternal);
+        c.abort = true;
+        return nullptr;
+    }
+    if (cp + sz > c.limit || (int64_t)((qb + 31) >> 5) * Wd * 32 > S.urow_words) {
         if (lane == 0) set_error(a, kErrArena);
         c.abort = true;
         return nullptr;
     }
     int key_bits = a.key_shift + (32 - __clz(mp));
+    uint64_t t_sort = tnow(a);
     warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, pn, key_bits);
+    if (lane == 0 && a.debug) {
+        tadd(a, c, 4, t_sort);
+        c.tm[8] += nQd;
+        c.tm[9] += pn;
+        c.tm[10] += 1;
+        c.tm[11] += mp;
+        c.tm[12] += (uint64_t)W;
+        c.tm[13] += (uint64_t)(nQ + nP);
+    }
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
-    Frame D = frame_at(cp, mp, nd, Wd);
-    for (int k = lane; k < qn; k += 32) D.gid[k] = F.gid[S.qsrc[k]];
-    for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
+    Frame D = frame_at(cp, mp, QWd, pn, Wd);
+    for (int k = lane; k < pn; k += 32) D.gid[k] = (int32_t)(S.pkey[k] & id_mask);
     compact_ids(c, F.Lid, Lw, W, D.Lid);
-    build_child_rows(c, F.rows, W, S.qsrc, qn, S.psrc, pn, D.rows, Wd);
+    build_child_rows(c, F.rows, W, nullptr, 0, S.psrc, pn, D.rows, Wd);
+    if (QWd > 0) {
+        zero_words(c, D.Q, (int64_t)mp * QWd);
+        if (nq1 > 0) q_child_columns(c, F.Q, QW, S.jlist, mp, D.Q, QWd);
+        if (qb > 0) {
+            // earlier P entries: their rows packed to L', then transposed into
+            // the columns after the inherited members
+            build_child_rows(c, F.rows, W, S.qsrc, qb, nullptr, 0, S.urows, Wd);
+            rows_to_columns(c, S.urows, Wd, nullptr, qb, mp, D.Q, QWd, nq1);
+        }
+    }
     if (a.emit) {
         int nr0 = F.h->nR;
         for (int k = lane; k < nr0; k += 32) D.R[k] = F.R[k];
@@ -613,7 +872,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         FrameHdr h;
         h.m = mp;
         h.W = Wd;
-        h.nQ = qn;
+        h.nQ = nQd;
         h.nP = pn;
         h.i = 0;
         h.end = pn;
@@ -621,7 +880,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         h.graph = F.h->graph;
         h.Rsum = Rs;
         h.nR = nRd;
-        h.depth = F.h->depth + 1;
+        h.QW = QWd;
         h.bytes = sz;
         h.parent = fp - c.arena;
         *D.h = h;
@@ -815,9 +1074,9 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         return false;
     }
 
-    const int nd = qn + pn;
+    const int QW = (qn + 63) >> 6;
     const int nRd = a.emit ? 1 + nfull : 0;
-    const int64_t sz = frame_bytes(d, nd, W, nRd);
+    const int64_t sz = frame_bytes(d, QW, pn, W, nRd);
     char *cp = c.arena;
     if (cp + sz > c.limit) {
         if (lane == 0) set_error(a, kErrArena);
@@ -827,11 +1086,15 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     int key_bits = a.key_shift + (32 - __clz(d));
     warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, pn, key_bits);
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
-    Frame D = frame_at(cp, d, nd, W);
-    for (int k = lane; k < qn; k += 32) D.gid[k] = S.ugid[S.qsrc[k]];
-    for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
+    Frame D = frame_at(cp, d, QW, pn, W);
+    for (int k = lane; k < pn; k += 32) D.gid[k] = (int32_t)(S.pkey[k] & id_mask);
     for (int k = lane; k < d; k += 32) D.Lid[k] = G.u_adj[ro + k];
-    build_child_rows(c, S.urows, W, S.qsrc, qn, S.psrc, pn, D.rows, W);
+    build_child_rows(c, S.urows, W, nullptr, 0, S.psrc, pn, D.rows, W);
+    if (QW > 0) {
+        // the earlier-ranked candidates, transposed into one column per vertex of N(r)
+        zero_words(c, D.Q, (int64_t)d * QW);
+        rows_to_columns(c, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
+    }
     if (a.emit) {
         if (lane == 0) D.R[0] = r;
         for (int k = lane; k < nfull; k += 32) D.R[1 + k] = S.rtmp[k];
@@ -848,7 +1111,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         h.graph = graph;
         h.Rsum = Rs;
         h.nR = nRd;
-        h.depth = 1;
+        h.QW = QW;
         h.bytes = sz;
         h.parent = -1;
         *D.h = h;
@@ -861,8 +1124,10 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
 // ---------------------------------------------------------------- stealing
 enum : int32_t { kSlotEmpty = 0, kSlotWriting = 1, kSlotFull = 2, kSlotTaken = 3 };
 
-__device__ void warp_copy(char *dst, const char *src, int64_t bytes, int lane, bool from_other_sm)
+__device__ bool warp_copy(char *dst, const char *src, int64_t bytes, int lane, bool from_other_sm)
 {
+    // frames are 16-byte aligned multiples of 16 bytes; anything else is a bug: copy nothing
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15) || (bytes & 15) || bytes < 0) return false;
     const int4 *s = reinterpret_cast<const int4 *>(src);
     int4 *d = reinterpret_cast<int4 *>(dst);
     int64_t n = bytes >> 4;
@@ -887,6 +1152,7 @@ __device__ void warp_copy(char *dst, const char *src, int64_t bytes, int lane, b
     }
     for (; k < n; k += 32) d[k] = from_other_sm ? __ldcg(s + k) : s[k];
     __syncwarp();
+    return true;
 }
 
 // If some worker is idle and this worker's slot is free, give away the upper
@@ -919,7 +1185,15 @@ __device__ void maybe_donate(const SearchArgs &a, Ctx &c, char *top)
             }
             __syncwarp();
             uint64_t t_cp = tnow(a);
-            warp_copy(slot, fp, h->bytes, lane, false);
+            if (!warp_copy(slot, fp, h->bytes, lane, false)) {
+                if (lane == 0) {
+                    set_error(a, kErrInternal);
+                    atomicExch(a.slot_state + c.wid, kSlotEmpty);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), ~0ULL);
+                }
+                c.abort = true;
+                return;
+            }
             if (lane == 0) tadd(a, c, 3, t_cp);
             if (lane == 0) {
                 FrameHdr *sh = reinterpret_cast<FrameHdr *>(slot);
@@ -979,7 +1253,14 @@ __device__ bool try_steal(const SearchArgs &a, Ctx &c)
                 return false;
             }
             uint64_t t_cp = tnow(a);
-            warp_copy(c.arena, slot, bytes, lane, true);
+            if (!warp_copy(c.arena, slot, bytes, lane, true)) {
+                if (lane == 0) {
+                    set_error(a, kErrInternal);
+                    atomicExch(a.slot_state + victim, kSlotEmpty);
+                }
+                c.abort = true;
+                return false;
+            }
             if (lane == 0) tadd(a, c, 3, t_cp);
             __threadfence();
             if (lane == 0) atomicExch(a.slot_state + victim, kSlotEmpty);
@@ -1014,7 +1295,7 @@ __device__ void run_stack(const SearchArgs &a, Ctx &c, char *top)
                 }
             }
             err = __shfl_sync(kFull, err, 0);
-            trace(a, c, 2, h->depth);
+            trace(a, c, 2, c.depth);
             if (err) {
                 c.abort = true;
                 break;
@@ -1051,7 +1332,10 @@ __device__ void finish_task(const SearchArgs &a, Ctx &c, int owner)
     __syncwarp();
 }
 
-__global__ void search_kernel(SearchArgs a)
+#ifndef MBE_SEARCH_MIN_BLOCKS
+#define MBE_SEARCH_MIN_BLOCKS 2 // resident 256-thread blocks per SM the register budget is sized for
+#endif
+__global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(SearchArgs a)
 {
     extern __shared__ uint32_t smem[];
     Ctx c;
@@ -1065,8 +1349,9 @@ __global__ void search_kernel(SearchArgs a)
     c.cm = reinterpret_cast<uint64_t *>(my + 256 + 32);
     c.lw = reinterpret_cast<uint64_t *>(my + 256 + 32 + 32 * 7 * 2);
     c.aw = reinterpret_cast<int32_t *>(my + 256 + 32 + 32 * 7 * 2 + 64);
+    c.sbuf = reinterpret_cast<uint64_t *>(my + 256 + 32 + 32 * 7 * 2 + 64 + 32);
     c.na = 0;
-    for (int q = 0; q < 8; ++q) c.tm[q] = 0;
+    for (int q = 0; q < 16; ++q) c.tm[q] = 0;
     c.arena = a.arena + (int64_t)c.wid * a.arena_bytes;
     c.mark = a.mark + (int64_t)c.wid * a.mark_stride;
     {
@@ -1087,9 +1372,18 @@ __global__ void search_kernel(SearchArgs a)
         c.s.ugid = reinterpret_cast<int32_t *>(q);
         q += pad16(4 * nc);
         c.s.pkey = reinterpret_cast<uint64_t *>(q);
-        q += 8 * nc;
+        q += pad16(8 * nc);
         c.s.pkey2 = reinterpret_cast<uint64_t *>(q);
-        q += 8 * nc;
+        q += pad16(8 * nc);
+        const int64_t qw = (nc + 63) / 64 + 1;
+        c.s.jlist = reinterpret_cast<int32_t *>(q);
+        q += pad16(4 * 2048);
+        c.s.mq = reinterpret_cast<uint64_t *>(q);
+        q += pad16(8 * qw);
+        c.s.offq = reinterpret_cast<int32_t *>(q);
+        q += pad16(4 * qw);
+        c.s.cmq = reinterpret_cast<uint64_t *>(q);
+        q += pad16(56 * qw);
         c.s.urows = reinterpret_cast<uint64_t *>(q);
         c.s.urow_words = a.urow_bytes / 8;
     }
@@ -1216,7 +1510,9 @@ int search_fit_shape(int threads, int blocks_per_sm_req)
     if (cudaFuncGetAttributes(&fa, search_kernel) != cudaSuccess) return 0;
     if (threads > fa.maxThreadsPerBlock) return -fa.maxThreadsPerBlock / 32 * 32;
     int smem = (threads / 32) * search_smem_per_warp();
-    cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    // the limit is a property of the kernel shared by every launch: keep it at
+    // the largest block's need (never lower it for a smaller block)
+    cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * search_smem_per_warp());
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, threads, smem) != cudaSuccess) return 0;
     return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;

@@ -22,7 +22,7 @@ _lock = threading.Lock()
 MBE_OK = 0
 STATUS = {0: "MBE_OK", 1: "MBE_ERR_INVALID_ARG", 2: "MBE_ERR_INVALID_GRAPH", 3: "MBE_ERR_OOM",
           4: "MBE_ERR_ARENA_FULL", 5: "MBE_ERR_OUTPUT_FULL", 6: "MBE_ERR_TIMEOUT", 7: "MBE_ERR_CUDA",
-          8: "MBE_ERR_UNSUPPORTED"}
+          8: "MBE_ERR_UNSUPPORTED", 9: "MBE_ERR_INTERNAL"}
 
 
 class MBEError(RuntimeError):
@@ -103,7 +103,8 @@ def load(build_if_missing: bool = True):
     global _lib
     with _lock:
         if _lib is None:
-            path = _build.build() if build_if_missing else _build.LIB
+            # MBE_LIBRARY points the binding at another build of the same sources
+            path = os.environ.get("MBE_LIBRARY") or (_build.build() if build_if_missing else _build.LIB)
             if not os.path.exists(path):
                 raise ImportError(f"CUDA library not built: {path}")
             lib = ctypes.CDLL(path)
