@@ -35,6 +35,29 @@ WORKLOAD_DESC = ("Chung-Lu bipartite |U|=20,000 |V|=50,000 |E|=200,000 exponents
                  "plain MBE (Algorithm 1), count + 64-bit hash")
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# search_kernel launch on the workload above, from the ncu capture summarised
+# in profiles/search_kernel_chunglu20k_dram.md, and the SHA-256 of the kernel
+# sources it was taken on; a kernel changed since then reports null.
+TRAFFIC = {"bytes": None, "sources_sha256": None}
+KERNEL_SOURCES = ("csrc/mbe_search.cu", "csrc/mbe_internal.h", "csrc/mbe_bits.h")
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2401_05039_gb300", rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def _traffic():
+    if TRAFFIC["bytes"] is None or TRAFFIC["sources_sha256"] != kernel_sources_sha256():
+        return None
+    return TRAFFIC["bytes"]
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -362,7 +385,7 @@ def run_mbe(args):
                        "nodes": int(r.nodes), "hash": hex(int(r.hash)), "workers": int(r.n_workers),
                        "l2": "flushed between steps (512 MB write)", "parallelism": f"replica x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm_peak, "traffic": _traffic(), "peak_kind": peak_kind,
                          "kernel": "search_kernel", "kernel_ms": kern, "bytes_alg_per_launch": int(np.mean(bytes_alg)),
                          "l2_copy_gbs_in_run": l2_gbs, "frac_of_l2_copy": achieved / l2_gbs},
             "cpu_baseline": cpu,

@@ -89,11 +89,15 @@ int mbe_graph_info(const mbe_graph *g, int32_t *nU, int32_t *nV, int64_t *nE, in
  * [5] steals, [6] elapsed ns, [8..13] ns in root setup, node scans, child
  * builds, frame copies, sorting, tasks; [14] root tasks, [15] stolen tasks,
  * [16..21] child builds: sum of |Q'|, sum of |P'|, builds, sum of |L'|, sum
- * of parent row words, sum of parent candidates. This copies up to
- * max_workers of them (24 uint64 each) to `host` and
+ * of parent row words, sum of parent candidates; [22] ns in the check
+ * against Q, [23] ns building child columns, of which [24] forming Q',
+ * [25] copying or compressing the parent's columns, [26] transposing P';
+ * [27] child builds that copied the columns uncompressed. This copies up to
+ * max_workers of them (MBE_TRACE_WORDS uint64 each) to `host` and
  * returns how many were copied. MBE_DEADLINE_MS bounds any single launch
  * (default 30 minutes); a launch past it stops with MBE_ERR_TIMEOUT.
  */
+#define MBE_TRACE_WORDS 32
 int mbe_debug_trace(uint64_t *host, int32_t max_workers);
 
 /* Free the current device's search workspace (the next call re-allocates it). */

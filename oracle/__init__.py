@@ -6,9 +6,9 @@ does. It shares no code with the GPU path.
 
 ``mbea_oracle.c`` holds the arithmetic (serial MBEA, per-root driver, batch
 driver, brute-force closure enumerator, SplitMix64 hash); this module only
-compiles it with gcc and marshals numpy arrays through ctypes. ``mlp.py``
-holds the float64 reference of the cost-model network and ``features.py``
-the per-root features and core numbers.
+compiles it with gcc and marshals numpy arrays through ctypes. ``learn.py``
+holds the per-root features, core numbers and the float64 reference of the
+cost-model network.
 """
 from __future__ import annotations
 

@@ -32,8 +32,15 @@ import synth  # noqa: E402
 GOLDEN = os.path.join(ROOT, "tests", "golden")
 
 
-def _row(r):
-    return {"count": int(r[0]), "hash": hex(int(r[1])), "nodes": int(r[2]), "bytes": int(r[3])}
+# Version of the algorithmic-byte model in oracle.bytes_node; progress files
+# written under another version keep valid counts, hashes and nodes only.
+BYTES_MODEL = 2
+
+
+def _row(r, with_bytes=True):
+    out = {"count": int(r[0]), "hash": hex(int(r[1])), "nodes": int(r[2])}
+    out["bytes"] = int(r[3]) if with_bytes else None
+    return out
 
 
 def _graph_info(g):
@@ -156,26 +163,38 @@ def prefix_sample(name, g, threads, seed=20240110, batch=256, keep_rows=300, pro
     live = np.nonzero(np.diff(g.u_off) > 0)[0]
     perm = rng.permutation(live).astype(np.int32)
     rows = np.zeros((0, 4), dtype=np.uint64)
+    model = BYTES_MODEL
     if progress and os.path.exists(progress):
         d = np.load(progress)
         if int(d["seed"]) == seed and d["digest"].item() == g.digest():
             rows = d["rows"]
+            model = int(d["bytes_model"]) if "bytes_model" in d else 1
     t0 = time.time()
     while rows.shape[0] < perm.size and (time_budget is None or time.time() - t0 < time_budget):
         k = rows.shape[0]
         part = oracle.per_root(g, roots=perm[k:k + batch], nthreads=threads)
         rows = np.concatenate([rows, part])
         if progress:
-            np.savez(progress + ".tmp.npz", rows=rows, seed=seed, digest=np.array(g.digest()))
+            np.savez(progress + ".tmp.npz", rows=rows, seed=seed, digest=np.array(g.digest()),
+                     bytes_model=np.array(model))
             os.replace(progress + ".tmp.npz", progress)
         print(f"{name}: {rows.shape[0]}/{perm.size} roots, {time.time() - t0:.0f}s", flush=True)
     K = rows.shape[0]
     pick = np.random.default_rng(seed + 1).choice(K, size=min(keep_rows, K), replace=False) if K else []
+    pick = sorted(int(x) for x in pick)
     total = rows.sum(axis=0, dtype=np.uint64) if K else np.zeros(4, np.uint64)
-    return {"workload": name, "graph": _graph_info(g), "total": _row(total) if K == perm.size else None,
-            "prefix": {"seed": seed, "k": int(K), "n_roots": int(perm.size), "sum": _row(total),
-                       "about": "sum over the first k roots of the seeded permutation of the non-isolated U vertices"},
-            "per_root": {str(int(perm[i])): _row(rows[i]) for i in sorted(int(x) for x in pick)},
+    fresh = model == BYTES_MODEL
+    if not fresh and pick:
+        # rows from an older byte model: the kept rows are run again, whole
+        again = oracle.per_root(g, roots=perm[pick], nthreads=threads)
+        assert (again[:, :3] == rows[pick, :3]).all(), "count/hash/nodes changed between oracle versions"
+        rows = rows.copy()
+        rows[pick] = again
+    return {"workload": name, "graph": _graph_info(g), "total": _row(total, fresh) if K == perm.size else None,
+            "prefix": {"seed": seed, "k": int(K), "n_roots": int(perm.size), "sum": _row(total, fresh),
+                       "about": "sum over the first k roots of the seeded permutation of the non-isolated U vertices"
+                                + ("" if fresh else "; bytes not stored: the sum was taken under an earlier byte model")},
+            "per_root": {str(int(perm[i])): _row(rows[i]) for i in pick},
             "oracle_threads": threads}
 
 

@@ -155,17 +155,22 @@ typedef struct {
 
 /*
  * Algorithmic bytes (the roofline numerator). Below the top level every
- * candidate row is the bit pattern of N(y) n L packed in 64-bit words, so a
- * node of a call with level set L reads ceil(|L|/64) words for x's row and
- * for every row it tests: all of Q (the check reads it to the end unless it
- * rejects; counted in full) and, when the node is maximal, the rest of P.
- * A top-level node instead reads the adjacency that builds the root's local
- * universe: N(r) and N(w) for every w in N(r), int32 each.
+ * candidate row is the bit pattern of N(y) n L packed in W = ceil(|L|/64)
+ * 64-bit words, and the same adjacency read the other way (reverse
+ * scanning, Section III-D) is one bitset over Q per vertex of L'. A node of
+ * a call with level set L reads x's row (W words); for the check against Q,
+ * the cheaper of all Q rows (W |Q| words) and the |L'| columns over Q
+ * (|L'| ceil(|Q|/64) words), counted in full; and, when the node is
+ * maximal, the rows of the rest of P (W each). A top-level node instead
+ * reads the adjacency that builds the root's local universe: N(r) and N(w)
+ * for every w in N(r), int32 each.
  */
-static uint64_t bytes_node(int64_t nL, int64_t nQ, int64_t n_rest, int maximal)
+static uint64_t bytes_node(int64_t nL, int64_t nLp, int64_t nQ, int64_t n_rest, int maximal)
 {
-    uint64_t words = (uint64_t)((nL + 63) / 64);
-    return 8ULL * words * (uint64_t)(1 + nQ + (maximal ? n_rest : 0));
+    const uint64_t W = (uint64_t)((nL + 63) / 64);
+    const uint64_t rows = W * (uint64_t)nQ;
+    const uint64_t cols = (uint64_t)nLp * (uint64_t)((nQ + 63) / 64);
+    return 8ULL * (W + (rows < cols ? rows : cols) + (maximal ? W * (uint64_t)n_rest : 0));
 }
 
 static void emit(oacc *acc, const ovec *L, const ovec *R)
@@ -249,7 +254,7 @@ static void mbea_iteration(const ograph *g, const ovec *L, const ovec *R, int32_
         for (int64_t k = 0; k < dx; ++k) b += 4ULL * (uint64_t)(g->v_off[Nx[k] + 1] - g->v_off[Nx[k]]);
         acc->bytes += b;
     } else {
-        acc->bytes += bytes_node(L->n, nQ, n_rest, is_maximal);
+        acc->bytes += bytes_node(L->n, Lp.n, nQ, n_rest, is_maximal);
     }
     goto done;
 oom:

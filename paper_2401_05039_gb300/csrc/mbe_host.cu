@@ -106,13 +106,13 @@ unsigned long long *debug_buffer(int n_warps)
         cudaFree(g_debug);
         g_debug = nullptr;
         g_debug_warps = 0;
-        if (cudaMalloc(&g_debug, sizeof(unsigned long long) * 24 * (size_t)n_warps) != cudaSuccess) {
+        if (cudaMalloc(&g_debug, sizeof(unsigned long long) * MBE_TRACE_WORDS * (size_t)n_warps) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
         g_debug_warps = n_warps;
     }
-    cudaMemset(g_debug, 0, sizeof(unsigned long long) * 24 * (size_t)n_warps);
+    cudaMemset(g_debug, 0, sizeof(unsigned long long) * MBE_TRACE_WORDS * (size_t)n_warps);
     return g_debug;
 }
 
@@ -616,7 +616,7 @@ int mbe_debug_trace(uint64_t *host, int32_t max_workers)
 {
     if (!g_debug || !host) return 0;
     int n = std::min(max_workers, g_debug_warps);
-    if (cudaMemcpy(host, g_debug, sizeof(uint64_t) * 24 * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    if (cudaMemcpy(host, g_debug, sizeof(uint64_t) * MBE_TRACE_WORDS * (size_t)n, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
     return n;
 }
 

@@ -91,8 +91,11 @@ inline int64_t scratch_layout_bytes(int64_t ncap, int64_t urow_bytes)
     return (b + 255) / 256 * 256;
 }
 
+// Bytes of a search frame's header.
+constexpr int64_t kFrameHdrBytes = 80;
+
 // Upper bound of the level-1 frame of a root of degree d with at most nc
-// candidates: header, L ids, Q columns (d x ceil(nc/64) words), P ids,
+// candidates: header, L ids, X columns (d x ceil(nc/64) words), P ids,
 // P rows (32-row tiles of ceil(d/64) words), R ids.
 #if defined(__CUDACC__)
 __host__ __device__
@@ -100,7 +103,7 @@ __host__ __device__
 inline int64_t level1_frame_bound(int64_t d, int64_t nc)
 {
     const int64_t W = (d + 63) / 64;
-    return 64 + (4 * d + 15) / 16 * 16 + (8 * d * ((nc + 63) / 64) + 15) / 16 * 16 + (4 * nc + 15) / 16 * 16 +
+    return kFrameHdrBytes + (4 * d + 15) / 16 * 16 + (8 * d * ((nc + 63) / 64) + 15) / 16 * 16 + (4 * nc + 15) / 16 * 16 +
            256 * W * ((nc + 31) / 32) + (4 * (nc + 1) + 15) / 16 * 16;
 }
 

@@ -17,17 +17,20 @@
 //  - its candidates P as rows packed to L (bit j = adjacency to the j-th
 //    vertex of L), 64-bit words, in tiles of 32 rows stored word-major so
 //    lane k of a warp reads row 32t+k with coalesced loads;
-//  - its inherited maximality-check set Q transposed, as m columns: column
-//    j is a bitset over Q of the members adjacent to the j-th vertex of L.
-//    "Some q in Q has N(q) >= L'" is then an AND of the |L'| columns of L'
-//    (the paper's reverse scanning, Section III-D: iterate over L' instead
-//    of Q), 64 candidates per word, stopping as soon as it is empty, and Q'
-//    is the OR of the same columns.
-// A child frame re-packs P' rows to L' and compresses the chosen Q columns
-// by the Q' mask (bit compression of mbe_bits.h), so deep frames stay small.
-// Expansion (Algorithm 1, step 4) and the check against the P entries
-// popped earlier are AND + popcount over P rows, one candidate per lane,
-// with warp ballots for rejection and prefix sums for compaction.
+//  - its check set X = Q followed by P (in pop order) transposed, as m
+//    columns: column j is a bitset over the positions of X of the members
+//    adjacent to the j-th vertex of L. When the i-th entry of P is popped,
+//    Algorithm 1's Q is exactly the prefix of nQ + i positions, so "some q
+//    in Q has N(q) >= L'" is an AND of the |L'| columns of L' over that
+//    prefix (the paper's reverse scanning, Section III-D: iterate over L'
+//    instead of Q), 64 candidates per word, stopping as soon as it is
+//    empty, and Q' is the OR of the same columns over the same prefix.
+// A child frame re-packs P' rows to L', compresses the chosen columns by
+// the Q' mask (bit compression of mbe_bits.h) and appends its own P' to
+// them by a warp bit-matrix transpose, so deep frames stay small.
+// Expansion (Algorithm 1, step 4) is AND + popcount over the later P rows,
+// one candidate per lane, with warp ballots and prefix sums for
+// compaction.
 //
 // Frames live on a per-warp stack in device memory (an arena slice); the
 // stack top is L1/L2 resident. P' is ordered by (|N(v) n L'|, id) once when
@@ -44,6 +47,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // active-word masks lw[32] u64, active-word indices aw[32] i32
 constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32 + 34 * 2;
 constexpr int kTiles = 4; // 32-row tiles whose loads a lane keeps in flight together
+// a child's Q' columns are compressed when that leaves at most 1/4 of the words
+constexpr int kCompressNum = 1, kCompressDen = 4;
+// roots whose neighbours' degrees sum to at least this order L by degree class
+constexpr int64_t kDegSortMin = 8192;
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
@@ -69,9 +76,9 @@ __device__ __forceinline__ uint64_t warp_sum64(uint64_t v)
 __device__ __forceinline__ int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
 
 struct __align__(16) FrameHdr {
-    int32_t m;       // |L|: bits per P row and number of Q columns
+    int32_t m;       // |L|: bits per P row and number of X columns
     int32_t W;       // 64-bit words per P row
-    int32_t nQ;      // inherited maximality-check candidates (bits per Q column)
+    int32_t nQ;      // |Q|: inherited maximality-check candidates
     int32_t nP;      // candidates to pop, sorted by (count, id)
     int32_t i;       // next P position to pop
     int32_t end;     // one past the last P position this worker pops
@@ -79,16 +86,19 @@ struct __align__(16) FrameHdr {
     int32_t graph;   // graph of the subtree
     uint64_t Rsum;   // sum of key_u over R
     int32_t nR;      // |R| stored in the frame (emit mode), else 0
-    int32_t QW;      // 64-bit words per Q column
+    int32_t QW;      // 64-bit words per X column
     int64_t bytes;   // size of the frame
     int64_t parent;  // offset of the parent frame from the arena base, -1 at the bottom
+    int32_t qpos;    // X positions before P (>= nQ: positions of no Q member are zero in every column)
+    int32_t copy_hint; // 1 when the last child built from this frame copied its columns uncompressed
+    int32_t pad_[2];
 };
-static_assert(sizeof(FrameHdr) == 64, "frame header is 64 bytes");
+static_assert(sizeof(FrameHdr) == kFrameHdrBytes, "frame header size");
 
 struct Frame {
     FrameHdr *h;
     int32_t *Lid;    // [m] vertex ids of L (V side)
-    uint64_t *Q;     // [m][QW] Q columns
+    uint64_t *Q;     // [m][QW] columns over X = Q then P (nQ + nP positions)
     int32_t *gid;    // [nP] P candidate ids (U side)
     uint64_t *rows;  // [ceil(nP/32)][W][32] P rows
     int32_t *R;      // [nR]
@@ -98,14 +108,14 @@ __device__ __forceinline__ int64_t frame_bytes(int m, int QW, int nP, int W, int
 {
     int64_t tiles = (nP + 31) >> 5;
     // every section is a multiple of 16 bytes: frames are copied with 16-byte accesses
-    return 64 + pad16(4LL * m) + pad16(8LL * m * QW) + pad16(4LL * nP) + 256LL * W * tiles + pad16(4LL * nR);
+    return kFrameHdrBytes + pad16(4LL * m) + pad16(8LL * m * QW) + pad16(4LL * nP) + 256LL * W * tiles + pad16(4LL * nR);
 }
 
 __device__ __forceinline__ Frame frame_at(char *p, int m, int QW, int nP, int W)
 {
     Frame f;
     f.h = reinterpret_cast<FrameHdr *>(p);
-    char *q = p + 64;
+    char *q = p + kFrameHdrBytes;
     f.Lid = reinterpret_cast<int32_t *>(q);
     q += pad16(4LL * m);
     f.Q = reinterpret_cast<uint64_t *>(q);
@@ -149,7 +159,7 @@ __device__ __forceinline__ GView gview(const SearchArgs &a, int g)
 
 // Scratch region of a warp's arena (top end), reused by every node.
 struct Scratch {
-    int32_t *qsrc;  // Q' source positions
+    int32_t *qsrc;  // root: universe positions of the earlier-ranked candidates
     int32_t *psrc;  // P' source positions
     uint64_t *pkey; // P' sort keys (count << key_shift | id)
     int32_t *psrc2;
@@ -160,7 +170,7 @@ struct Scratch {
     uint64_t *mq;   // Q' mask over the inherited Q (one word per 64 candidates)
     int32_t *offq;  // exclusive prefix of popcount(mq) per word
     uint64_t *cmq;  // compress stage masks of every mq word (6 per word)
-    uint64_t *urows;// root universe rows; child rows of earlier P entries at other nodes
+    uint64_t *urows;// root universe rows
     int64_t ncap;   // capacity of the lists
     int64_t urow_words;
 };
@@ -179,7 +189,7 @@ struct Ctx {
     int32_t *aw;      // shared [32]: their word indices
     uint64_t *sbuf;   // shared [34]: staging of compressed Q column words
     int na;           // number of nonzero words of L'
-    uint64_t tm[16];  // debug: ns in root setup, scans, child build, copies, sort, busy; counters
+    unsigned long long *dbg; // this worker's progress record (tracing runs only, else null)
     uint64_t cnt, hash, nodes, bytes; // current task (uniform across lanes)
     uint64_t t_cnt, t_hash, t_nodes, t_bytes, t_don, t_steal;
     int since_check;
@@ -191,8 +201,8 @@ struct Ctx {
 // Progress record of a worker (debug builds of a run only).
 __device__ __forceinline__ void trace(const SearchArgs &a, const Ctx &c, int phase, long long arg)
 {
-    if (a.debug && c.lane == 0) {
-        unsigned long long *d = a.debug + 24LL * c.wid;
+    if (c.dbg && c.lane == 0) {
+        unsigned long long *d = c.dbg;
         d[0] = (unsigned long long)phase;
         d[1] = (unsigned long long)arg;
         d[2] = c.t_nodes + c.nodes;
@@ -200,7 +210,6 @@ __device__ __forceinline__ void trace(const SearchArgs &a, const Ctx &c, int pha
         d[4] = c.t_don;
         d[5] = c.t_steal;
         d[6] = globaltimer() - c.t_start;
-        for (int q = 0; q < 16; ++q) d[8 + q] = c.tm[q];
     }
 }
 
@@ -211,7 +220,7 @@ __device__ __forceinline__ uint64_t tnow(const SearchArgs &a)
 }
 __device__ __forceinline__ void tadd(const SearchArgs &a, Ctx &c, int b, uint64_t since)
 {
-    if (a.debug) c.tm[b] += globaltimer() - since;
+    if (c.dbg) c.dbg[8 + b] += globaltimer() - since;
 }
 
 __device__ __forceinline__ bool past_deadline(const SearchArgs &a, const Ctx &c)
@@ -412,17 +421,16 @@ __device__ __forceinline__ void prepare_masks(Ctx &c, uint64_t Lw, int W)
 // source tile array, compressed to the bits of L' (masks from prepare_masks,
 // active words from set_active_words). Source words are gathered four at a
 // time before they are compressed.
-__device__ void build_child_rows(Ctx &c, const uint64_t *srows, int Ws, const int32_t *qsrc, int qn,
-                                 const int32_t *psrc, int pn, uint64_t *drows, int Wd)
+__device__ void build_child_rows(Ctx &c, const uint64_t *srows, int Ws, const int32_t *psrc, int n,
+                                 uint64_t *drows, int Wd)
 {
     const int lane = c.lane;
-    const int n = qn + pn;
     const int na = c.na;
     const int32_t *off = c.off;
     for (int t0 = 0; t0 < n; t0 += 32) {
         int k = t0 + lane;
         bool valid = k < n;
-        int s = valid ? (k < qn ? qsrc[k] : psrc[k - qn]) : 0;
+        int s = valid ? psrc[k] : 0;
         const uint64_t *src = srows + row_word(s, 0, Ws);
         uint64_t cur = 0;
         int o = 0;
@@ -531,54 +539,121 @@ __device__ __forceinline__ void bit_positions(Ctx &c, uint64_t Lw, int W, int32_
     __syncwarp();
 }
 
-// True when some inherited q has N(q) >= L': the AND of the columns listed
-// in J is nonempty. Four words per lane in flight; a 128-word chunk stops as
-// soon as its running AND is empty.
-__device__ bool q_any_superset(const Ctx &c, const uint64_t *Q, int QW, const int32_t *J, int mp)
+// True when some position p < lim of X has N(p) >= L': the AND of the
+// columns listed in J (stride QW words), over the first LW = ceil(lim/64)
+// words with the last one cut by `last`, is nonempty. Two columns of four
+// words per lane in flight; a 128-word chunk stops as soon as its running
+// AND is empty.
+__device__ bool q_any_superset(const Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J,
+                               int mp)
 {
     const int lane = c.lane;
-    for (int w0 = 0; w0 < QW; w0 += 128) {
+    for (int w0 = 0; w0 < LW; w0 += 128) {
         uint64_t acc[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[k] = (w0 + 32 * k + lane < QW) ? ~0ULL : 0ULL;
-        int jreg = 0;
-        for (int t = 0; t < mp; ++t) {
-            if ((t & 31) == 0) jreg = t + lane < mp ? J[t + lane] : 0;
-            const int j = __shfl_sync(kFull, jreg, t & 31);
-            const uint64_t *col = Q + (int64_t)j * QW + w0 + lane;
-            uint64_t x[4];
+        for (int k = 0; k < 4; ++k) {
+            const int w = w0 + 32 * k + lane;
+            acc[k] = w < LW ? (w == LW - 1 ? last : ~0ULL) : 0ULL;
+        }
+        for (int t = 0; t < mp; t += 2) {
+            const bool two = t + 1 < mp;
+            const uint64_t *col0 = Q + (int64_t)J[t] * QW + w0 + lane;
+            const uint64_t *col1 = Q + (int64_t)J[two ? t + 1 : t] * QW + w0 + lane;
+            uint64_t x[4], y[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) x[k] = (w0 + 32 * k + lane < QW) ? col[32 * k] : 0ULL;
+            for (int k = 0; k < 4; ++k) {
+                const bool ok = w0 + 32 * k + lane < LW;
+                x[k] = ok ? col0[32 * k] : 0ULL;
+                y[k] = ok ? col1[32 * k] : 0ULL;
+            }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) acc[k] &= x[k];
-            if ((t & 3) == 3 && !__any_sync(kFull, (acc[0] | acc[1] | acc[2] | acc[3]) != 0)) break;
+            for (int k = 0; k < 4; ++k) acc[k] &= x[k] & y[k];
+            if (!__any_sync(kFull, (acc[0] | acc[1] | acc[2] | acc[3]) != 0)) break;
         }
         if (__any_sync(kFull, (acc[0] | acc[1] | acc[2] | acc[3]) != 0)) return true;
     }
     return false;
 }
 
-// Q' over the inherited Q: mq = OR of the columns listed in J, offq = its
-// per-word exclusive popcount prefix, cmq = its compress stage masks.
-// Returns |Q'| (inherited part).
-__device__ int q_union_mask(Ctx &c, const uint64_t *Q, int QW, const int32_t *J, int mp)
+// Q' over the prefix of X: mq = OR of the columns listed in J (stride QW)
+// over the first LW words, the last cut by `last`. Eight loads per lane in
+// flight. Returns |Q'|.
+__device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp)
+{
+    const int lane = c.lane;
+    Scratch &S = c.s;
+    int total = 0;
+    for (int w0 = 0; w0 < LW; w0 += 32) {
+        const int w = w0 + lane;
+        const bool v = w < LW;
+        const uint64_t *base = Q + (v ? w : 0);
+        uint64_t m = 0;
+        int jreg = 0;
+        for (int t = 0; t < mp; t += 8) {
+            if ((t & 31) == 0) jreg = t + lane < mp ? J[t + lane] : 0;
+            uint64_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = __shfl_sync(kFull, jreg, (t + k) & 31);
+                x[k] = (v && t + k < mp) ? base[(int64_t)j * QW] : 0ULL;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) m |= x[k];
+        }
+        if (w == LW - 1) m &= last;
+        if (v) S.mq[w] = m;
+        total += __popcll(m);
+    }
+    __syncwarp();
+    return (int)__reduce_add_sync(kFull, (unsigned)total);
+}
+
+// q_union and, fused with it, the uncompressed child columns of
+// q_copy_columns (every word loaded once, stored as it is OR-ed).
+__device__ int q_union_copy(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
+                            uint64_t *dst, int QWd)
+{
+    const int lane = c.lane;
+    Scratch &S = c.s;
+    int total = 0;
+    for (int w0 = 0; w0 < QWd; w0 += 32) {
+        const int w = w0 + lane;
+        const bool v = w < LW;
+        const bool vd = w < QWd;
+        const uint64_t cut = w == LW - 1 ? last : ~0ULL;
+        const uint64_t *base = Q + (v ? w : 0);
+        uint64_t m = 0;
+        for (int t = 0; t < mp; t += 8) {
+            uint64_t x[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int j = t + k < mp ? J[t + k] : 0;
+                x[k] = (v && t + k < mp) ? (base[(int64_t)j * QW] & cut) : 0ULL;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                m |= x[k];
+                if (vd && t + k < mp) dst[(int64_t)(t + k) * QWd + w] = x[k];
+            }
+        }
+        if (v) S.mq[w] = m;
+        total += __popcll(m);
+    }
+    __syncwarp();
+    return (int)__reduce_add_sync(kFull, (unsigned)total);
+}
+
+// Compression of the prefix by mq: offq = per-word exclusive popcount
+// prefix, cmq = compress stage masks of every word.
+__device__ void q_compress_masks(Ctx &c, int LW)
 {
     const int lane = c.lane;
     Scratch &S = c.s;
     int run = 0;
-    for (int w0 = 0; w0 < QW; w0 += 32) {
+    for (int w0 = 0; w0 < LW; w0 += 32) {
         const int w = w0 + lane;
-        const bool v = w < QW;
-        const uint64_t *base = Q + (v ? w : 0);
-        uint64_t m0 = 0, m1 = 0;
-        int t = 0;
-        for (; t + 2 <= mp; t += 2) {
-            const uint64_t x0 = base[(int64_t)J[t] * QW], x1 = base[(int64_t)J[t + 1] * QW];
-            m0 |= x0;
-            m1 |= x1;
-        }
-        if (t < mp) m0 |= base[(int64_t)J[t] * QW];
-        const uint64_t m = v ? (m0 | m1) : 0ULL;
+        const bool v = w < LW;
+        const uint64_t m = v ? S.mq[w] : 0ULL;
         const int pc = __popcll(m);
         int incl = pc;
 #pragma unroll
@@ -587,7 +662,6 @@ __device__ int q_union_mask(Ctx &c, const uint64_t *Q, int QW, const int32_t *J,
             if (lane >= o) incl += y;
         }
         if (v) {
-            S.mq[w] = m;
             S.offq[w] = run + incl - pc;
             CompressMasks cm = compress_prepare(m);
 #pragma unroll
@@ -596,26 +670,61 @@ __device__ int q_union_mask(Ctx &c, const uint64_t *Q, int QW, const int32_t *J,
         run += __shfl_sync(kFull, incl, 31);
     }
     __syncwarp();
-    return run;
 }
 
-// Child Q column t = parent column J[t] compressed by mq, for every t < mp:
-// each 32-word chunk of the parent column is compressed lane-wise and
-// assembled in shared memory, then written out; only the first word of a
-// chunk can hold bits of the previous chunk (it is OR-ed). dst is zeroed.
-__device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, const int32_t *J, int mp, uint64_t *dst,
+// Child column t = the first LW words of parent column J[t] (stride QW),
+// last word cut by `last`, copied without compression: positions outside Q'
+// are zero in every column of L' already. Words [LW, QWd) are zeroed for
+// the P' bits that follow.
+__device__ void q_copy_columns(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
+                               uint64_t *dst, int QWd)
+{
+    const int lane = c.lane;
+    // mp * QWd words: the frame fits the stack, far below 2^31 words
+    const unsigned total = (unsigned)mp * (unsigned)QWd;
+    for (unsigned b = 0; b < total; b += 128) {
+        uint64_t x[4];
+        int64_t di[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const unsigned idx = b + 32 * u + lane;
+            di[u] = -1;
+            x[u] = 0;
+            if (idx < total) {
+                const int t = (int)(idx / (unsigned)QWd);
+                const int w = (int)(idx - (unsigned)t * (unsigned)QWd);
+                di[u] = idx;
+                if (w < LW) {
+                    x[u] = Q[(int64_t)J[t] * QW + w];
+                    if (w == LW - 1) x[u] &= last;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (di[u] >= 0) dst[di[u]] = x[u];
+    }
+    __syncwarp();
+}
+
+// Child column t = the first LW words of parent column J[t] (stride QW)
+// compressed by mq, for every t < mp: each 32-word chunk of the parent
+// column is compressed lane-wise and assembled in shared memory, then
+// written out; only the first word of a chunk can hold bits of the previous
+// chunk (it is OR-ed). dst is zeroed.
+__device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, int LW, const int32_t *J, int mp, uint64_t *dst,
                                 int QWd)
 {
     const int lane = c.lane;
     Scratch &S = c.s;
-    if (QW <= 8) {
+    if (LW <= 8) {
         // short columns: one lane per child column, bits appended in registers
         for (int t = lane; t < mp; t += 32) {
             const uint64_t *col = Q + (int64_t)J[t] * QW;
             uint64_t *out = dst + (int64_t)t * QWd;
             uint64_t cur = 0;
             int o = 0, b = 0;
-            for (int w = 0; w < QW; ++w) {
+            for (int w = 0; w < LW; ++w) {
                 CompressMasks cm;
                 cm.m = S.mq[w];
 #pragma unroll
@@ -640,9 +749,9 @@ __device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, const int32_t
     for (int t = 0; t < mp; ++t) {
         const uint64_t *col = Q + (int64_t)J[t] * QW;
         uint64_t *out = dst + (int64_t)t * QWd;
-        for (int w0 = 0; w0 < QW; w0 += 32) {
+        for (int w0 = 0; w0 < LW; w0 += 32) {
             const int w = w0 + lane;
-            const bool v = w < QW;
+            const bool v = w < LW;
             uint64_t val = 0;
             int nb = 0, off = 0;
             if (v) {
@@ -656,7 +765,7 @@ __device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, const int32_t
             }
             const int first = __shfl_sync(kFull, off, 0);
             const int k0 = first >> 6;
-            const int last_lane = min(31, QW - 1 - w0);
+            const int last_lane = min(31, LW - 1 - w0);
             const int end_bit = __shfl_sync(kFull, off + nb, last_lane);
             if (end_bit == first) continue;
             const int k1 = (end_bit - 1) >> 6;
@@ -677,9 +786,37 @@ __device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, const int32_t
     }
 }
 
+// Transpose of a 32 x 32 bit matrix held one row per lane (bit c of lane
+// r's word = entry (r, c)): afterwards lane c holds column c (bit r = entry
+// (r, c)). Recursive block transpose: at each of the five levels, lanes
+// that differ in bit s swap the off-diagonal s x s blocks by one shuffle.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+    constexpr uint32_t kMask[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int s = 16 >> k;
+        const uint32_t m = kMask[k];
+        const uint32_t y = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~m) | ((y >> s) & m)) : ((x & m) | ((y & m) << s));
+    }
+    return x;
+}
+
+// ORs 32 bits (rows t0..t0+31 of one column) into a column at bit p.
+__device__ __forceinline__ void or_bits32(uint64_t *col, int p, uint32_t v)
+{
+    if (!v) return;
+    uint64_t *cw = col + (p >> 6);
+    const int b = p & 63;
+    cw[0] |= (uint64_t)v << b;
+    if (b > 32 && ((uint64_t)v >> (64 - b)) != 0) cw[1] |= (uint64_t)v >> (64 - b);
+}
+
 // Transposes n rows (tile layout, Wr words, row k taken from position
 // pos[k] or k) into ncols column bitsets of QWd words, writing the rows as
-// bits bit0 .. bit0+n-1 of every column (OR into zeroed columns).
+// bits bit0 .. bit0+n-1 of every column (OR into zeroed columns). Each
+// 32-row x 64-column block is two warp transposes.
 __device__ void rows_to_columns(Ctx &c, const uint64_t *rows, int Wr, const int32_t *pos, int n, int ncols,
                                 uint64_t *cols, int QWd, int bit0)
 {
@@ -689,23 +826,14 @@ __device__ void rows_to_columns(Ctx &c, const uint64_t *rows, int Wr, const int3
         const bool valid = k < n;
         const int src = valid ? (pos ? pos[k] : k) : 0;
         const uint64_t *r = rows + row_word(src, 0, Wr);
-        for (int jb = 0; jb < ncols; jb += 32) {
-            const uint64_t x = valid ? r[(jb >> 6) * 32] : 0ULL;
-            const int sh = jb & 63;
-            unsigned mine = 0;
-            const int nq = min(32, ncols - jb);
-            for (int q = 0; q < nq; ++q) {
-                const unsigned bal = __ballot_sync(kFull, (x >> (sh + q)) & 1ULL);
-                if (lane == q) mine = bal;
-            }
-            const int colj = jb + lane;
-            if (colj < ncols && mine) {
-                const int p = bit0 + t0;
-                uint64_t *cw = cols + (int64_t)colj * QWd + (p >> 6);
-                const int b = p & 63;
-                cw[0] |= (uint64_t)mine << b;
-                if (b > 32 && ((uint64_t)mine >> (64 - b)) != 0) cw[1] |= (uint64_t)mine >> (64 - b);
-            }
+        const int p = bit0 + t0;
+        for (int w = 0; w * 64 < ncols; ++w) {
+            const uint64_t x = valid ? r[w * 32] : 0ULL;
+            const uint32_t lo = warp_transpose32((uint32_t)x, lane);
+            const uint32_t hi = warp_transpose32((uint32_t)(x >> 32), lane);
+            const int c0 = w * 64 + lane, c1 = c0 + 32;
+            if (c0 < ncols) or_bits32(cols + (int64_t)c0 * QWd, p, lo);
+            if (c1 < ncols) or_bits32(cols + (int64_t)c1 * QWd, p, hi);
         }
     }
     __syncwarp();
@@ -740,31 +868,24 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     set_active_words(c, Lw);
     prepare_offsets(c, Lw, W);
     Scratch &S = c.s;
-    bit_positions(c, Lw, W, S.jlist);
+    int32_t *J = S.jlist;
+    bit_positions(c, Lw, W, J);
 
-    // Step 3: maximality check: the inherited Q (columns), then the P
-    // entries popped before x (rows, positions [0, i)).
-    bool rejected = nQ > 0 && q_any_superset(c, F.Q, QW, S.jlist, mp);
-    int qb = 0;
-    const int q_end = (i + 31) >> 5;
-    for (int t0 = 0; t0 < q_end && !rejected; t0 += kTiles) {
-        int cnt[kTiles];
-        count_tiles<kTiles>(c, F.rows, W, t0, q_end, cnt);
-#pragma unroll
-        for (int u = 0; u < kTiles; ++u) {
-            const int k = (t0 + u) * 32 + lane;
-            const bool valid = (t0 + u < q_end) && k < i;
-            if (__ballot_sync(kFull, valid && cnt[u] == mp)) {
-                rejected = true;
-                break;
-            }
-            const bool part = valid && cnt[u] > 0;
-            const unsigned bal = __ballot_sync(kFull, part);
-            if (part) S.qsrc[qb + __popc(bal & lanemask_lt())] = k;
-            qb += __popc(bal);
-        }
+    // Step 3: maximality check against Algorithm 1's Q at this iteration:
+    // the inherited Q and the P entries popped before x, i.e. the first
+    // nQ + i positions of X (columns).
+    const uint64_t t_q = tnow(a);
+    const int lim = F.h->qpos + i;
+    const int LW = (lim + 63) >> 6;
+    const uint64_t last = (lim & 63) ? ((1ULL << (lim & 63)) - 1) : ~0ULL;
+    const bool rejected = lim > 0 && q_any_superset(c, F.Q, QW, LW, last, J, mp);
+    if (lane == 0) tadd(a, c, 14, t_q);
+    {
+        // algorithmic bytes: x's row, the cheaper of the Q rows and the L'
+        // columns over Q (|Q| = nQ + i here), and the later P rows when maximal
+        const uint64_t nq = (uint64_t)(nQ + i), rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
+        c.bytes += 8ULL * ((uint64_t)W + (rows < cols ? rows : cols) + (rejected ? 0ULL : (uint64_t)W * (nP - i - 1)));
     }
-    c.bytes += 8ULL * (uint64_t)W * (uint64_t)(1 + nQ + i + (rejected ? 0 : (nP - i - 1)));
     if (rejected) {
         if (lane == 0) tadd(a, c, 1, t_scan);
         return nullptr;
@@ -815,22 +936,46 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         return nullptr;
     }
 
-    // Child frame: Q' (inherited members touching L', then the earlier P
-    // entries with 0 < count < |L'|) as columns over L', P' rows sorted by
-    // (count, id), all packed to L'.
+    // Child frame: Q' (the members of the prefix touching L') as columns
+    // over L', then P' rows sorted by (count, id), all packed to L'; the
+    // child's X is Q' followed by P'. Q' is compressed to its members when
+    // that shrinks the columns to at most kCompressNum/kCompressDen of the
+    // prefix, else the prefix is copied with its holes.
     const int Wd = (mp + 63) >> 6;
-    const int nq1 = nQ > 0 ? q_union_mask(c, F.Q, QW, S.jlist, mp) : 0;
-    const int nQd = nq1 + qb;
-    const int QWd = (nQd + 63) >> 6;
     const int nRd = a.emit ? F.h->nR + 1 + nfull : 0;
-    const int64_t sz = frame_bytes(mp, QWd, pn, Wd, nRd);
     char *cp = fp + F.h->bytes;
-    if (((uintptr_t)cp & 15) || (sz & 15)) {
+    if ((uintptr_t)cp & 15) {
         if (lane == 0) set_error(a, kErrInternal);
         c.abort = true;
         return nullptr;
     }
-    if (cp + sz > c.limit || (int64_t)((qb + 31) >> 5) * Wd * 32 > S.urow_words) {
+    uint64_t t_qc = tnow(a);
+    // When the previous child of this frame was copied, this one is copied
+    // while Q' is formed (one pass over the words), before the choice.
+    const int QWcopy = (lim + pn + 63) >> 6;
+    const bool spec = lim > 0 && F.h->copy_hint != 0 && cp + frame_bytes(mp, QWcopy, pn, Wd, nRd) <= c.limit;
+    uint64_t *dQ = reinterpret_cast<uint64_t *>(cp + kFrameHdrBytes + pad16(4LL * mp));
+    int nQd = 0;
+    if (spec)
+        nQd = q_union_copy(c, F.Q, QW, LW, last, J, mp, dQ, QWcopy);
+    else if (lim > 0)
+        nQd = q_union(c, F.Q, QW, LW, last, J, mp);
+    const bool compress = kCompressDen * ((nQd + 63) >> 6) <= kCompressNum * LW;
+    if (lane == 0) F.h->copy_hint = compress ? 0 : 1;
+    if (compress && nQd > 0) q_compress_masks(c, LW);
+    if (lane == 0) {
+        tadd(a, c, 15, t_qc);
+        tadd(a, c, 16, t_qc);
+    }
+    const int qposd = compress ? nQd : lim;
+    const int QWd = (qposd + pn + 63) >> 6;
+    const int64_t sz = frame_bytes(mp, QWd, pn, Wd, nRd);
+    if (sz & 15) {
+        if (lane == 0) set_error(a, kErrInternal);
+        c.abort = true;
+        return nullptr;
+    }
+    if (cp + sz > c.limit) {
         if (lane == 0) set_error(a, kErrArena);
         c.abort = true;
         return nullptr;
@@ -838,29 +983,35 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     int key_bits = a.key_shift + (32 - __clz(mp));
     uint64_t t_sort = tnow(a);
     warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, pn, key_bits);
-    if (lane == 0 && a.debug) {
+    if (lane == 0 && c.dbg) {
         tadd(a, c, 4, t_sort);
-        c.tm[8] += nQd;
-        c.tm[9] += pn;
-        c.tm[10] += 1;
-        c.tm[11] += mp;
-        c.tm[12] += (uint64_t)W;
-        c.tm[13] += (uint64_t)(nQ + nP);
+        c.dbg[16] += nQd;
+        c.dbg[17] += pn;
+        c.dbg[18] += 1;
+        c.dbg[19] += mp;
+        c.dbg[20] += (uint64_t)W;
+        c.dbg[21] += (uint64_t)(nQ + nP);
     }
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
     Frame D = frame_at(cp, mp, QWd, pn, Wd);
     for (int k = lane; k < pn; k += 32) D.gid[k] = (int32_t)(S.pkey[k] & id_mask);
     compact_ids(c, F.Lid, Lw, W, D.Lid);
-    build_child_rows(c, F.rows, W, nullptr, 0, S.psrc, pn, D.rows, Wd);
-    if (QWd > 0) {
+    build_child_rows(c, F.rows, W, S.psrc, pn, D.rows, Wd);
+    t_qc = tnow(a);
+    if (compress) {
         zero_words(c, D.Q, (int64_t)mp * QWd);
-        if (nq1 > 0) q_child_columns(c, F.Q, QW, S.jlist, mp, D.Q, QWd);
-        if (qb > 0) {
-            // earlier P entries: their rows packed to L', then transposed into
-            // the columns after the inherited members
-            build_child_rows(c, F.rows, W, S.qsrc, qb, nullptr, 0, S.urows, Wd);
-            rows_to_columns(c, S.urows, Wd, nullptr, qb, mp, D.Q, QWd, nq1);
-        }
+        if (nQd > 0) q_child_columns(c, F.Q, QW, LW, J, mp, D.Q, QWd);
+    } else if (!spec) {
+        q_copy_columns(c, F.Q, QW, LW, last, J, mp, D.Q, QWd);
+    }
+    const uint64_t t_tr = tnow(a);
+    rows_to_columns(c, D.rows, Wd, nullptr, pn, mp, D.Q, QWd, qposd);
+    if (lane == 0 && c.dbg) {
+        const uint64_t now = globaltimer();
+        c.dbg[23] += now - t_qc;
+        c.dbg[25] += t_tr - t_qc;
+        c.dbg[26] += now - t_tr;
+        c.dbg[27] += compress ? 0 : 1;
     }
     if (a.emit) {
         int nr0 = F.h->nR;
@@ -883,6 +1034,9 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         h.QW = QWd;
         h.bytes = sz;
         h.parent = fp - c.arena;
+        h.qpos = qposd;
+        h.copy_hint = 1;
+        h.pad_[0] = h.pad_[1] = 0;
         *D.h = h;
         tadd(a, c, 2, t_build);
     }
@@ -915,7 +1069,33 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     Scratch &S = c.s;
     int32_t *mark = c.mark;
 
-    // Discovery: for every (j, w = N(r)[j]) and u in N(w), u != r, give u a
+    // L = N(r) in ascending order of degree class (floor log2): column j of
+    // every frame below is then about as sparse as the ones after it or
+    // more, so the AND of a check meets its sparsest columns first and
+    // empties early. Any order of L is valid (L is a set); it is applied
+    // only when the root's candidate lists can be long (sum of the degrees
+    // of N(r) at least kDegSortMin), and needs room in the lists.
+    const int32_t *Ln = G.u_adj + ro;
+    if (d > 1 && d <= S.ncap) {
+        int64_t sdeg = 0;
+        for (int j = lane; j < d; j += 32) {
+            const int w = G.u_adj[ro + j];
+            const int dw = G.v_off[w + 1] - G.v_off[w];
+            sdeg += dw;
+            S.pkey[j] = ((uint64_t)min(31 - __clz(max(dw, 1)), 15) << 11) | (uint64_t)j;
+            S.psrc[j] = w;
+        }
+        sdeg = (int64_t)warp_sum64((uint64_t)sdeg);
+        __syncwarp();
+        if (sdeg >= kDegSortMin) {
+            warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, d, 15);
+            for (int j = lane; j < d; j += 32) S.jlist[j] = S.psrc[j];
+            __syncwarp();
+            Ln = S.jlist;
+        }
+    }
+
+    // Discovery: for every (j, w = L[j]) and u in N(w), u != r, give u a
     // local id and set bit j of its row. Pairs are flattened across up to
     // 32 consecutive w so that lanes stay busy when degrees are small.
     int nc = 0, zeroed = 0;
@@ -923,7 +1103,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     for (int j0 = 0; j0 < d; j0 += 32) {
         int j = j0 + lane;
         bool vj = j < d;
-        int w = vj ? G.u_adj[ro + j] : 0;
+        int w = vj ? Ln[j] : 0;
         int wo = vj ? G.v_off[w] : 0;
         int wd = vj ? G.v_off[w + 1] - wo : 0;
         int incl = wd;
@@ -1036,7 +1216,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     rsum = warp_sum64(rsum);
     const uint64_t Rs = key_u(r) + rsum;
     uint64_t ls = 0;
-    for (int j = lane; j < d; j += 32) ls += key_v(G.u_adj[ro + j]);
+    for (int j = lane; j < d; j += 32) ls += key_v(Ln[j]);
     ls = warp_sum64(ls);
     if (first) {
         c.cnt += 1;
@@ -1064,7 +1244,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
                 o[2] = r;
             }
             for (int k = lane; k < nfull; k += 32) o[3 + k] = S.rtmp[k];
-            for (int k = lane; k < d; k += 32) o[2 + nR + k] = G.u_adj[ro + k];
+            for (int k = lane; k < d; k += 32) o[2 + nR + k] = Ln[k];
         } else if (lane == 0) {
             set_error(a, MBE_ERR_OUTPUT_FULL);
         }
@@ -1074,7 +1254,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         return false;
     }
 
-    const int QW = (qn + 63) >> 6;
+    const int QW = (qn + pn + 63) >> 6;
     const int nRd = a.emit ? 1 + nfull : 0;
     const int64_t sz = frame_bytes(d, QW, pn, W, nRd);
     char *cp = c.arena;
@@ -1088,13 +1268,13 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
     Frame D = frame_at(cp, d, QW, pn, W);
     for (int k = lane; k < pn; k += 32) D.gid[k] = (int32_t)(S.pkey[k] & id_mask);
-    for (int k = lane; k < d; k += 32) D.Lid[k] = G.u_adj[ro + k];
-    build_child_rows(c, S.urows, W, nullptr, 0, S.psrc, pn, D.rows, W);
-    if (QW > 0) {
-        // the earlier-ranked candidates, transposed into one column per vertex of N(r)
-        zero_words(c, D.Q, (int64_t)d * QW);
-        rows_to_columns(c, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
-    }
+    for (int k = lane; k < d; k += 32) D.Lid[k] = Ln[k];
+    build_child_rows(c, S.urows, W, S.psrc, pn, D.rows, W);
+    // X = the earlier-ranked candidates, then P in pop order, transposed
+    // into one column per vertex of N(r)
+    zero_words(c, D.Q, (int64_t)d * QW);
+    if (qn > 0) rows_to_columns(c, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
+    rows_to_columns(c, D.rows, W, nullptr, pn, d, D.Q, QW, qn);
     if (a.emit) {
         if (lane == 0) D.R[0] = r;
         for (int k = lane; k < nfull; k += 32) D.R[1 + k] = S.rtmp[k];
@@ -1114,6 +1294,9 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         h.QW = QW;
         h.bytes = sz;
         h.parent = -1;
+        h.qpos = qn;
+        h.copy_hint = 1;
+        h.pad_[0] = h.pad_[1] = 0;
         *D.h = h;
         tadd(a, c, 0, t_root);
     }
@@ -1351,7 +1534,7 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(Sear
     c.aw = reinterpret_cast<int32_t *>(my + 256 + 32 + 32 * 7 * 2 + 64);
     c.sbuf = reinterpret_cast<uint64_t *>(my + 256 + 32 + 32 * 7 * 2 + 64 + 32);
     c.na = 0;
-    for (int q = 0; q < 16; ++q) c.tm[q] = 0;
+    c.dbg = a.debug ? a.debug + (int64_t)MBE_TRACE_WORDS * c.wid : nullptr;
     c.arena = a.arena + (int64_t)c.wid * a.arena_bytes;
     c.mark = a.mark + (int64_t)c.wid * a.mark_stride;
     {
@@ -1428,7 +1611,7 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(Sear
             if (pushed && !c.abort) run_stack(a, c, c.arena);
             if (c.lane == 0) {
                 tadd(a, c, 5, t_busy);
-                c.tm[6] += 1;
+                if (c.dbg) c.dbg[14] += 1;
             }
             finish_task(a, c, a.per_root_mode == 2 ? g : r);
             if (c.abort) break;
@@ -1447,7 +1630,7 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(Sear
             run_stack(a, c, c.arena);
             if (c.lane == 0) {
                 tadd(a, c, 5, t_busy);
-                c.tm[7] += 1;
+                if (c.dbg) c.dbg[15] += 1;
             }
             finish_task(a, c, owner);
             if (c.abort) break;
