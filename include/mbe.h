@@ -184,6 +184,11 @@ typedef struct {
     int32_t n_exec;           /* length of exec_order */
     const void *class_params; /* mbe_enumerate_batch: const mbe_class_params[MBE_N_CLASSES] from
                                  mbe_autotune_batch, or NULL for the defaults */
+    int32_t layout;           /* search frame layout (no counterpart in the paper; the result does not
+                                 depend on it): 1 = rows (every candidate's row over L; checks stop at
+                                 the first superset row), 2 = columns (Q and P as one bitset per vertex
+                                 of L: checks are ANDs of the |L'| columns), 0 = auto: columns when some
+                                 V vertex has at least 256 neighbours, else rows */
 } mbe_options;
 
 /* Fill *opt with the defaults (all "auto"). */
@@ -242,6 +247,8 @@ typedef struct {
     int32_t blocks_per_sm; /* 0 = default */
     int32_t steal;         /* frame donation on/off for this class */
     int32_t valid;         /* 0: the class uses the defaults */
+    int32_t layout;        /* frame layout as mbe_options.layout (0 = auto) */
+    int32_t reserved;
     double tuned_ms;       /* time the autotuner measured for this choice on its sample */
 } mbe_class_params;
 
@@ -251,7 +258,7 @@ int mbe_batch_class(int32_t nU, int32_t nV, int64_t nE);
 /*
  * Autotuner (no counterpart in the paper): for every size class present in
  * the batch, times a set of launch shapes (block size, blocks per SM,
- * stealing on/off) on an evenly spaced sample of the class (at least
+ * stealing on/off, frame layout rows/columns) on an evenly spaced sample of the class (at least
  * sample_per_class graphs and enough graphs for 16 roots per worker, or the
  * whole class) and writes the fastest into table[class] (valid = 1).
  * Arguments as in mbe_enumerate_batch; table has MBE_N_CLASSES entries.

@@ -120,6 +120,7 @@ struct ClassPlan {
     std::vector<int32_t> troot, tgraph;
     int64_t nc_max = 0, urow_max = 0, frame_max = 0;
     int32_t max_nU = 1;
+    int32_t max_deg_v = 0; // largest V degree of the class's graphs (automatic layout choice)
 };
 
 void plan_class(const HostBatch &b, const DeviceBatch &d, const std::vector<int32_t> &graphs, ClassPlan &p)
@@ -148,6 +149,8 @@ void plan_class(const HostBatch &b, const DeviceBatch &d, const std::vector<int3
         p.urow_max = std::max<int64_t>(p.urow_max, (int64_t)d.hb[4 * (size_t)gi + 1]);
         p.frame_max = std::max<int64_t>(p.frame_max, (int64_t)d.hb[4 * (size_t)gi + 2]);
         p.max_nU = std::max(p.max_nU, b.nU[gi]);
+        const int32_t *vo = b.v_off_cat + b.v_off_start[gi];
+        for (int32_t v = 0; v < b.nV[gi]; ++v) p.max_deg_v = std::max(p.max_deg_v, vo[v + 1] - vo[v]);
     }
 }
 
@@ -156,14 +159,14 @@ struct ClassLaunch {
     int steal;
 };
 
-ClassLaunch launch_for(const mbe_class_params *prm, const mbe_options &o)
+ClassLaunch launch_for(const mbe_class_params *prm, const mbe_options &o, const ClassPlan &p)
 {
     ClassLaunch c;
     if (prm && prm->valid) {
-        c.shape = shape_for(prm->block_threads, prm->blocks_per_sm);
+        c.shape = shape_for(prm->block_threads, prm->blocks_per_sm, resolve_layout(prm->layout, p.max_deg_v));
         c.steal = prm->steal ? 1 : 0;
     } else {
-        c.shape = shape_for(o.block_threads, o.blocks_per_sm);
+        c.shape = shape_for(o.block_threads, o.blocks_per_sm, resolve_layout(o.layout, p.max_deg_v));
         c.steal = o.steal ? 1 : 0;
     }
     return c;
@@ -193,7 +196,7 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
     Workspace &ws = device_workspace();
     int64_t nc = 0, urow = 0, frame = 0, n_tasks = 0;
     int32_t max_nU = 1;
-    LaunchShape big = cl.empty() ? shape_for(0, 0) : cl[0].shape;
+    LaunchShape big = cl.empty() ? shape_for(0, 0, kLayoutColumns) : cl[0].shape;
     for (size_t k = 0; k < plans.size(); ++k) {
         nc = std::max(nc, plans[k].nc_max);
         urow = std::max(urow, plans[k].urow_max);
@@ -283,7 +286,7 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
             for (size_t k = 0; k < plans.size() && r == cudaSuccess; ++k) {
                 if (args[k].n_tasks == 0) continue;
                 r = cudaMemsetAsync(ws.slot_state, 0, sizeof(int32_t) * (size_t)ws.n_warps, q);
-                if (r == cudaSuccess) r = launch_search(args[k], blocks[k], cl[k].shape.threads, q);
+                if (r == cudaSuccess) r = launch_layout(args[k], blocks[k], cl[k].shape, q);
             }
             return r;
         };
@@ -373,6 +376,10 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
     mbe_options o;
     mbe_default_options(&o);
     if (opts) o = *opts;
+    if (o.layout < 0 || o.layout > kLayoutColumns) return set_status(total, MBE_ERR_INVALID_ARG);
+    const mbe_class_params *tab = static_cast<const mbe_class_params *>(o.class_params);
+    for (int k = 0; tab && k < MBE_N_CLASSES; ++k)
+        if (tab[k].valid && (tab[k].layout < 0 || tab[k].layout > kLayoutColumns)) return set_status(total, MBE_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     DeviceBatch d;
     st = upload(b, d, s);
@@ -392,8 +399,8 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
         p.cls = k;
         plan_class(b, d, members[k], p);
         if (p.troot.empty()) continue;
+        cl.push_back(launch_for(table ? table + k : nullptr, o, p));
         plans.push_back(std::move(p));
-        cl.push_back(launch_for(table ? table + k : nullptr, o));
     }
     double ms = 0.0;
     uint64_t don = 0;
@@ -450,8 +457,11 @@ int mbe_autotune_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t 
     }
     mbe_options o;
     mbe_default_options(&o);
-    // candidate launch shapes: (threads, blocks per SM, steal)
-    const int cand[][3] = {{64, 8, 1}, {128, 4, 1}, {256, 2, 1}, {512, 1, 1}, {256, 1, 1}, {128, 4, 0}, {256, 2, 0}};
+    // candidates: (threads, blocks per SM, steal, frame layout)
+    const int cand[][4] = {{64, 8, 1, kLayoutRows},     {128, 4, 1, kLayoutRows},    {256, 2, 1, kLayoutRows},
+                           {512, 1, 1, kLayoutRows},    {256, 2, 0, kLayoutRows},    {64, 8, 1, kLayoutColumns},
+                           {128, 4, 1, kLayoutColumns}, {256, 2, 1, kLayoutColumns}, {512, 1, 1, kLayoutColumns},
+                           {256, 2, 0, kLayoutColumns}};
     const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
     std::vector<std::vector<int32_t>> members(MBE_N_CLASSES);
     for (int32_t i = 0; i < n_graphs; ++i)
@@ -467,7 +477,7 @@ int mbe_autotune_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t 
         // the sample must fill the GPU, or it measures launch overhead
         // instead of throughput: at least sample_per_class graphs and at
         // least 16 roots per default worker, spread evenly over the class
-        const int64_t want_roots = 16LL * shape_for(0, 0).warps;
+        const int64_t want_roots = 16LL * shape_for(0, 0, kLayoutColumns).warps;
         int64_t class_roots = (int64_t)full.troot.size();
         size_t m = std::min<size_t>((size_t)sample_per_class, order.size());
         if (class_roots > 0) {
@@ -482,8 +492,8 @@ int mbe_autotune_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t 
         if (plans[0].troot.empty()) continue;
         double best = 1e300;
         for (int c = 0; c < n_cand && st == MBE_OK; ++c) {
-            mbe_class_params prm{cand[c][0], cand[c][1], cand[c][2], 1, 0.0};
-            std::vector<ClassLaunch> cl(1, launch_for(&prm, o));
+            mbe_class_params prm{cand[c][0], cand[c][1], cand[c][2], 1, cand[c][3], 0, 0.0};
+            std::vector<ClassLaunch> cl(1, launch_for(&prm, o, plans[0]));
             double ms = 0.0, ms2 = 0.0;
             st = run_classes(d, plans, cl, o, s, false, &ms, nullptr); // warm-up
             if (st == MBE_OK) st = run_classes(d, plans, cl, o, s, false, &ms2, nullptr);

@@ -123,29 +123,46 @@ int key_bits_for(int64_t n)
     return b;
 }
 
-LaunchShape shape_for(int block_threads, int blocks_per_sm)
+int resolve_layout(int32_t requested, int32_t max_deg_v)
+{
+    if (requested == kLayoutRows || requested == kLayoutColumns) return requested;
+    return max_deg_v >= kColumnsMinDegV ? kLayoutColumns : kLayoutRows;
+}
+
+LaunchShape shape_for(int block_threads, int blocks_per_sm, int layout)
 {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto fit_shape = layout == kLayoutRows ? search_rows_fit_shape : search_fit_shape;
     int threads = block_threads > 0 ? block_threads : 256;
     threads = std::max(32, std::min(1024, threads / 32 * 32));
     int per_sm = blocks_per_sm > 0 ? blocks_per_sm : std::max(1, 512 / threads); // 16 warps per SM by default
-    int fit = search_fit_shape(threads, per_sm);
+    int fit = fit_shape(threads, per_sm);
     if (fit < 0) { // block too large for the kernel's register use
         threads = -fit;
         per_sm = blocks_per_sm > 0 ? blocks_per_sm : std::max(1, 512 / threads);
-        fit = search_fit_shape(threads, per_sm);
+        fit = fit_shape(threads, per_sm);
     }
     if (fit > 0) per_sm = fit;
     LaunchShape s;
     s.threads = threads;
     s.blocks = sms * per_sm;
     s.warps = s.blocks * (threads / 32);
+    s.layout = layout == kLayoutRows ? kLayoutRows : kLayoutColumns;
     return s;
 }
 
-LaunchShape choose_shape(const mbe_options &o) { return shape_for(o.block_threads, o.blocks_per_sm); }
+LaunchShape choose_shape(const mbe_options &o, int layout)
+{
+    return shape_for(o.block_threads, o.blocks_per_sm, layout);
+}
+
+cudaError_t launch_layout(const SearchArgs &a, int blocks, const LaunchShape &shape, cudaStream_t s)
+{
+    return shape.layout == kLayoutRows ? launch_search_rows(a, blocks, shape.threads, s)
+                                       : launch_search(a, blocks, shape.threads, s);
+}
 
 // Sizes (and allocates when needed) the per-warp workspace for a launch.
 int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t frame_max, int32_t max_nU,
@@ -219,7 +236,7 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
 int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStream_t s, mbe_result *out,
                mbe_biclique_buffer *bic)
 {
-    LaunchShape shape = choose_shape(o);
+    LaunchShape shape = choose_shape(o, in.layout);
     int stack_factor = 2;
     for (int attempt = 0; attempt < 4; ++attempt) {
         int st = ensure_workspace(ws, in.nc_max, in.urow_max, in.frame_max, in.max_nU, shape, o.arena_bytes,
@@ -287,7 +304,7 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         MBE_TRY(cudaEventCreate(&e0));
         MBE_TRY(cudaEventCreate(&e1));
         cudaEventRecord(e0, s);
-        cudaError_t le = launch_search(a, blocks, shape.threads, s);
+        cudaError_t le = launch_layout(a, blocks, shape, s);
         cudaEventRecord(e1, s);
         Ctl h;
         cudaError_t ce = cudaMemcpyAsync(&h, ws.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
@@ -330,7 +347,8 @@ int root_features(mbe_graph *g, float *d_feat, int32_t *d_raw, cudaStream_t s)
     Workspace &ws = device_workspace();
     mbe_options o;
     mbe_default_options(&o);
-    int st = ensure_workspace(ws, g->nc_max, g->urow_max, g->frame_max, g->nU, choose_shape(o), 0, 2);
+    int st = ensure_workspace(ws, g->nc_max, g->urow_max, g->frame_max, g->nU,
+                              choose_shape(o, resolve_layout(o.layout, g->max_deg_v)), 0, 2);
     if (st != MBE_OK) return st;
     const int n = g->nU + g->nV;
     int32_t *tmp = nullptr, *raw = nullptr;
@@ -422,7 +440,8 @@ int learned_schedule(mbe_graph *g, const mbe_model *md, bool presplit, cudaStrea
                 if (std::isfinite(pred[u]) && pred[u] > 0.f) total += std::expm1((double)pred[u]);
             mbe_options o;
             mbe_default_options(&o);
-            const double share = total / std::max(1, choose_shape(o).warps);
+            const double share =
+                total / std::max(1, choose_shape(o, resolve_layout(o.layout, g->max_deg_v)).warps);
             for (int k = 0; k < head; ++k) {
                 const int r = top[k];
                 const double pn = std::expm1((double)pred[r]);
@@ -659,7 +678,8 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     if (o.emit && (!bicliques->ids || !bicliques->offsets || bicliques->capacity_ids < 0 ||
                    bicliques->capacity_bicliques < 0))
         return set_status(out, MBE_ERR_INVALID_ARG);
-    if (o.block_threads < 0 || o.blocks_per_sm < 0 || o.watchdog_ms < 0 || o.arena_bytes < 0)
+    if (o.block_threads < 0 || o.blocks_per_sm < 0 || o.watchdog_ms < 0 || o.arena_bytes < 0 || o.layout < 0 ||
+        o.layout > kLayoutColumns)
         return set_status(out, MBE_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     if (g->nU == 0 || g->n_live == 0) return set_status(out, MBE_OK);
@@ -710,6 +730,7 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     in.per_owner = reinterpret_cast<unsigned long long *>(o.per_root);
     in.n_owner = g->nU;
     in.per_mode = 1;
+    in.layout = resolve_layout(o.layout, g->max_deg_v);
     int st = run_search(device_workspace(), in, o, s, out, bicliques);
     if (out) out->prep_ms = prep_ms;
     return set_status(out, st);

@@ -118,4 +118,16 @@ int search_smem_per_warp();
 // kernel's limit and t is the largest allowed block size.
 int search_fit_shape(int threads, int blocks_per_sm_req);
 
+// The same three for the row-layout search kernel (mbe_search_rows.cu).
+cudaError_t launch_search_rows(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
+int search_rows_smem_per_warp();
+int search_rows_fit_shape(int threads, int blocks_per_sm_req);
+
+// Frame layouts of the two search kernels.
+enum : int32_t { kLayoutAuto = 0, kLayoutRows = 1, kLayoutColumns = 2 };
+
+// Automatic choice: the column layout when some V vertex has at least this
+// many neighbours (Q sets stay long at depth), else the row layout.
+constexpr int32_t kColumnsMinDegV = 256;
+
 } // namespace mbe

@@ -50,6 +50,7 @@ struct Workspace {
 
 struct LaunchShape {
     int threads, blocks, warps;
+    int layout; // kLayoutRows or kLayoutColumns: which search kernel
 };
 
 struct RunInput {
@@ -64,6 +65,7 @@ struct RunInput {
     unsigned long long *per_owner; // [n_owner][4], zeroed here before every launch
     int64_t n_owner;
     int32_t per_mode;
+    int32_t layout = kLayoutColumns; // resolved frame layout (kLayoutRows / kLayoutColumns)
 };
 
 
@@ -75,8 +77,12 @@ int64_t round_up(int64_t x, int64_t a);
 int key_bits_for(int64_t n);
 long long deadline_ms();
 unsigned long long *debug_buffer(int n_warps);
-LaunchShape shape_for(int block_threads, int blocks_per_sm);
-LaunchShape choose_shape(const mbe_options &o);
+// kLayoutRows / kLayoutColumns for a requested layout (0 = auto by the
+// largest V degree of the graphs searched).
+int resolve_layout(int32_t requested, int32_t max_deg_v);
+LaunchShape shape_for(int block_threads, int blocks_per_sm, int layout);
+LaunchShape choose_shape(const mbe_options &o, int layout);
+cudaError_t launch_layout(const SearchArgs &a, int blocks, const LaunchShape &shape, cudaStream_t s);
 int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t frame_max, int32_t max_nU,
                      const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor);
 int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStream_t s, mbe_result *out,

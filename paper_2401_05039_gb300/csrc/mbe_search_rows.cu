@@ -1,0 +1,1255 @@
+// Persistent warp-worker search kernel, row layout (the alternative to the
+// column layout of mbe_search.cu; the host picks one per launch).
+//
+// Each warp is an independent worker that runs Algorithm 1 (MBEA, paper
+// Section II-B) depth first over one task at a time:
+//  - a root task is one iteration of the top-level while loop: candidate r
+//    with L = V, Q = the top-level candidates popped before r and P = those
+//    after it, in the order (degree, id) (Section II-C, candidate
+//    selection: ascending |N(v) n L|, which is the degree when L = V);
+//  - a stolen task is a suffix of one frame's remaining candidates, split
+//    off by a busy worker when another worker is idle (Section III-C's
+//    work stealing, here without grid-wide synchronisation).
+//
+// Data layout (replaces the paper's compact arrays and lookup tables,
+// Section III-B and III-D): a root builds its local universe, the rows
+// bit(N(u) n N(r)) over the positions of N(r) for every u in N2(r). Every
+// frame stores the rows of all its candidates, Q then P, packed to its own
+// level set L (bit j of a row = adjacency to the j-th vertex of L), 64-bit
+// words, in tiles of 32 rows stored word-major so that lane k of a warp
+// reads row 32t+k with coalesced loads. A child frame re-packs the rows of
+// its candidates to L' with the bit compression of mbe_bits.h, so deep
+// frames are mostly one word per row. Maximality checking and maximal
+// expansion (Algorithm 1, steps 3 and 4) are AND + popcount over these
+// rows, one candidate per lane, four 32-row tiles of loads in flight, with
+// a warp ballot for the early rejection and prefix sums (ballot + popc) for
+// the compaction of Q' and P'. A check stops at the first superset row, so
+// this layout suits graphs whose Q sets stay short; the column layout suits
+// graphs with high-degree V vertices, whose Q sets stay long at depth.
+//
+// Frames live on a per-warp stack in device memory (an arena slice); the
+// stack top is L1/L2 resident. P' is ordered by (|N(v) n L'|, id) once when
+// its frame is pushed, which is the order in which Algorithm 1 pops it
+// because the counts are fixed while L' is fixed.
+#include "mbe_bits.h"
+#include "mbe_internal.h"
+
+namespace mbe {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+// per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
+// active-word masks lw[32] u64, active-word indices aw[32] i32
+constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32;
+constexpr int kTiles = 4; // 32-row tiles whose loads a lane keeps in flight together
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint64_t globaltimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t warp_sum64(uint64_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__device__ __forceinline__ int64_t pad16(int64_t b) { return (b + 15) & ~(int64_t)15; }
+
+struct __align__(16) FrameHdr {
+    int32_t m;       // |L|: bits per row
+    int32_t W;       // 64-bit words per row
+    int32_t nQ;      // inherited maximality-check candidates (positions 0..nQ-1)
+    int32_t nP;      // candidates to pop, sorted (positions nQ..nQ+nP-1)
+    int32_t i;       // next P position to pop
+    int32_t end;     // one past the last P position this worker pops
+    int32_t root;    // top-level candidate of this subtree (graph-local id)
+    int32_t graph;   // graph of the subtree
+    uint64_t Rsum;   // sum of key_u over R
+    int32_t nR;      // |R| stored in the frame (emit mode), else 0
+    int32_t depth;
+    int64_t bytes;   // size of the frame
+    int64_t parent;  // offset of the parent frame from the arena base, -1 at the bottom
+};
+static_assert(sizeof(FrameHdr) == 64, "frame header is 64 bytes");
+
+struct Frame {
+    FrameHdr *h;
+    int32_t *Lid;    // [m] vertex ids of L (V side)
+    int32_t *gid;    // [n] candidate ids (U side)
+    uint64_t *rows;  // [ceil(n/32)][W][32]
+    int32_t *R;      // [nR]
+};
+
+__device__ __forceinline__ int64_t frame_bytes(int m, int n, int W, int nR)
+{
+    int64_t tiles = (n + 31) >> 5;
+    return 64 + pad16(4LL * m) + pad16(4LL * n) + 256LL * W * tiles + pad16(4LL * nR);
+}
+
+__device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W)
+{
+    Frame f;
+    f.h = reinterpret_cast<FrameHdr *>(p);
+    char *q = p + 64;
+    f.Lid = reinterpret_cast<int32_t *>(q);
+    q += pad16(4LL * m);
+    f.gid = reinterpret_cast<int32_t *>(q);
+    q += pad16(4LL * n);
+    f.rows = reinterpret_cast<uint64_t *>(q);
+    q += 256LL * W * ((n + 31) >> 5);
+    f.R = reinterpret_cast<int32_t *>(q);
+    return f;
+}
+
+__device__ __forceinline__ Frame frame_of(char *p)
+{
+    const FrameHdr *h = reinterpret_cast<const FrameHdr *>(p);
+    return frame_at(p, h->m, h->nQ + h->nP, h->W);
+}
+
+__device__ __forceinline__ int64_t row_word(int k, int w, int W)
+{
+    return ((int64_t)(k >> 5) * W + w) * 32 + (k & 31);
+}
+
+struct GView {
+    const int32_t *u_off, *u_adj, *v_off, *v_adj;
+    int32_t nU, nV;
+};
+
+__device__ __forceinline__ GView gview(const SearchArgs &a, int g)
+{
+    GraphDesc d = a.graphs[g];
+    GView v;
+    v.u_off = a.u_off + d.u_off_base;
+    v.v_off = a.v_off + d.v_off_base;
+    v.u_adj = a.u_adj + d.edge_base;
+    v.v_adj = a.v_adj + d.edge_base;
+    v.nU = d.nU;
+    v.nV = d.nV;
+    return v;
+}
+
+// Scratch region of a warp's arena (top end), reused by every node.
+struct Scratch {
+    int32_t *qsrc;  // Q' source positions
+    int32_t *psrc;  // P' source positions
+    uint64_t *pkey; // P' sort keys (count << key_shift | id)
+    int32_t *psrc2;
+    uint64_t *pkey2;
+    int32_t *rtmp;  // ids that join R' (emit)
+    int32_t *ugid;  // root universe: candidate ids
+    uint64_t *urows;// root universe rows
+    int64_t ncap;   // capacity of the lists
+    int64_t urow_words;
+};
+
+struct Ctx {
+    int lane;
+    int wid;
+    char *arena;
+    char *limit;  // frames must end at or below this address
+    Scratch s;
+    int32_t *mark;
+    uint32_t *hist;   // shared [256]: radix-sort histogram
+    int32_t *off;     // shared [32]: bit offset of each L' word's first selected bit
+    uint64_t *cm;     // shared [32][7]: per word mask + 6 compress stage masks
+    uint64_t *lw;     // shared [32]: the nonzero words of L', in order
+    int32_t *aw;      // shared [32]: their word indices
+    int na;           // number of nonzero words of L'
+    unsigned long long *dbg; // this worker's progress record (tracing runs only, else null)
+    uint64_t cnt, hash, nodes, bytes; // current task (uniform across lanes)
+    uint64_t t_cnt, t_hash, t_nodes, t_bytes, t_don, t_steal;
+    int since_check;
+    bool abort;
+    uint64_t t_start; // globaltimer at kernel entry
+    int depth;        // current stack depth (progress record)
+};
+
+// Progress record of a worker (debug builds of a run only).
+__device__ __forceinline__ void trace(const SearchArgs &a, const Ctx &c, int phase, long long arg)
+{
+    if (c.dbg && c.lane == 0) {
+        unsigned long long *d = c.dbg;
+        d[0] = (unsigned long long)phase;
+        d[1] = (unsigned long long)arg;
+        d[2] = c.t_nodes + c.nodes;
+        d[3] = (unsigned long long)c.depth;
+        d[4] = c.t_don;
+        d[5] = c.t_steal;
+        d[6] = globaltimer() - c.t_start;
+    }
+}
+
+// debug phase timer: ns since `since` added to bucket b (lane 0 only; no-op without tracing)
+__device__ __forceinline__ uint64_t tnow(const SearchArgs &a)
+{
+    return a.debug ? globaltimer() : 0;
+}
+__device__ __forceinline__ void tadd(const SearchArgs &a, Ctx &c, int b, uint64_t since)
+{
+    if (c.dbg) c.dbg[8 + b] += globaltimer() - since;
+}
+
+__device__ __forceinline__ bool past_deadline(const SearchArgs &a, const Ctx &c)
+{
+    return (long long)(globaltimer() - c.t_start) > a.deadline_ns;
+}
+
+__device__ __forceinline__ void set_error(const SearchArgs &a, int code)
+{
+    atomicCAS(a.error, 0, code);
+}
+
+// ------------------------------------------------------------------ sorting
+// Ascending sort of n (key, value) pairs held in scratch; result in (k0, v0).
+// n <= 32: bitonic network in registers; larger: LSD radix sort, 8-bit
+// digits, stable scatter by warp ranking (match_any + popc).
+__device__ void warp_sort(Ctx &c, uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v1, int n, int key_bits)
+{
+    const int lane = c.lane;
+    if (n <= 1) return;
+    if (n <= 32) {
+        uint64_t key = lane < n ? k0[lane] : ~0ULL;
+        int32_t val = lane < n ? v0[lane] : 0;
+#pragma unroll
+        for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                uint64_t ok = __shfl_xor_sync(kFull, key, stride);
+                int32_t ov = __shfl_xor_sync(kFull, val, stride);
+                bool up = (lane & size) == 0;
+                bool lower = (lane & stride) == 0;
+                bool want_min = (lower == up);
+                bool take = want_min ? (ok < key) : (ok > key);
+                if (take) {
+                    key = ok;
+                    val = ov;
+                }
+            }
+        }
+        if (lane < n) {
+            k0[lane] = key;
+            v0[lane] = val;
+        }
+        __syncwarp();
+        return;
+    }
+    int passes = (key_bits + 7) / 8;
+    uint32_t *hist = c.hist;
+    for (int pass = 0; pass < passes; ++pass) {
+        int shift = pass * 8;
+        for (int b = lane; b < 256; b += 32) hist[b] = 0;
+        __syncwarp();
+        for (int t0 = 0; t0 < n; t0 += 32) {
+            int k = t0 + lane;
+            if (k < n) atomicAdd(&hist[(k0[k] >> shift) & 255], 1u);
+        }
+        __syncwarp();
+        // exclusive scan of the 256 bins: lane l owns bins 8l..8l+7
+        uint32_t loc[8], s = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            loc[j] = hist[lane * 8 + j];
+            s += loc[j];
+        }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        uint32_t run = incl - s;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            hist[lane * 8 + j] = run;
+            run += loc[j];
+        }
+        __syncwarp();
+        for (int t0 = 0; t0 < n; t0 += 32) {
+            int k = t0 + lane;
+            bool valid = k < n;
+            uint64_t key = valid ? k0[k] : 0;
+            int32_t val = valid ? v0[k] : 0;
+            int d = valid ? (int)((key >> shift) & 255) : 256 + lane;
+            unsigned peers = __match_any_sync(kFull, d);
+            int rank = __popc(peers & lanemask_lt());
+            uint32_t base = valid ? hist[d] : 0;
+            __syncwarp();
+            if (valid) {
+                k1[base + rank] = key;
+                v1[base + rank] = val;
+                if (rank == 0) hist[d] = base + __popc(peers);
+            }
+            __syncwarp();
+        }
+        uint64_t *tk = k0;
+        k0 = k1;
+        k1 = tk;
+        int32_t *tv = v0;
+        v0 = v1;
+        v1 = tv;
+    }
+    if (passes & 1) { // result is in the second buffer: copy back
+        for (int k = lane; k < n; k += 32) {
+            k1[k] = k0[k];
+            v1[k] = v0[k];
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- row scans
+// Publishes the nonzero words of L' (lane w holds word w) as a compact list.
+__device__ __forceinline__ void set_active_words(Ctx &c, uint64_t Lw)
+{
+    const unsigned act = __ballot_sync(kFull, Lw != 0);
+    if (Lw != 0) {
+        int pos = __popc(act & lanemask_lt());
+        c.aw[pos] = c.lane;
+        c.lw[pos] = Lw;
+    }
+    c.na = __popc(act);
+    __syncwarp();
+}
+
+// cnt[u] = popcount(row & L') for row 32*(t0+u) + lane, u < T, over the
+// nonzero words of L'. All loads of two words x T tiles are issued before
+// they are consumed, so a lane keeps 2T independent loads in flight.
+template <int T>
+__device__ __forceinline__ void count_tiles(const Ctx &c, const uint64_t *rows, int W, int t0, int t_end,
+                                            int (&cnt)[T])
+{
+#pragma unroll
+    for (int u = 0; u < T; ++u) cnt[u] = 0;
+    const uint64_t *base = rows + (int64_t)t0 * W * 32 + c.lane;
+    const int64_t ts = (int64_t)W * 32;
+    const int na = c.na;
+    int wi = 0;
+    for (; wi + 2 <= na; wi += 2) {
+        const int w0 = c.aw[wi], w1 = c.aw[wi + 1];
+        const uint64_t m0 = c.lw[wi], m1 = c.lw[wi + 1];
+        uint64_t x0[T], x1[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) {
+            const bool ok = t0 + u < t_end;
+            x0[u] = ok ? base[u * ts + w0 * 32] : 0ULL;
+            x1[u] = ok ? base[u * ts + w1 * 32] : 0ULL;
+        }
+#pragma unroll
+        for (int u = 0; u < T; ++u) cnt[u] += __popcll(x0[u] & m0) + __popcll(x1[u] & m1);
+    }
+    if (wi < na) {
+        const int w0 = c.aw[wi];
+        const uint64_t m0 = c.lw[wi];
+        uint64_t x0[T];
+#pragma unroll
+        for (int u = 0; u < T; ++u) x0[u] = (t0 + u < t_end) ? base[u * ts + w0 * 32] : 0ULL;
+#pragma unroll
+        for (int u = 0; u < T; ++u) cnt[u] += __popcll(x0[u] & m0);
+    }
+}
+
+// ------------------------------------------------------------- child frames
+// Lane w (< W) holds word w of L' in Lw. Publishes per-word compress masks
+// and the bit offset of every word's first selected bit in shared memory.
+__device__ __forceinline__ void prepare_masks(Ctx &c, uint64_t Lw, int W)
+{
+    int pc = __popcll(Lw);
+    int incl = pc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(kFull, incl, o);
+        if (c.lane >= o) incl += y;
+    }
+    if (c.lane < W) {
+        CompressMasks cm = compress_prepare(Lw);
+        uint64_t *dst = c.cm + c.lane * 7;
+        dst[0] = Lw;
+#pragma unroll
+        for (int i = 0; i < 6; ++i) dst[1 + i] = cm.mv[i];
+        c.off[c.lane] = incl - pc; // bit offset of word w
+    }
+    __syncwarp();
+}
+
+// Writes the rows of a child frame: row k' is source row src(k') of the
+// source tile array, compressed to the bits of L' (masks from prepare_masks,
+// active words from set_active_words). Source words are gathered four at a
+// time before they are compressed.
+__device__ void build_child_rows(Ctx &c, const uint64_t *srows, int Ws, const int32_t *qsrc, int qn,
+                                 const int32_t *psrc, int pn, uint64_t *drows, int Wd)
+{
+    const int lane = c.lane;
+    const int n = qn + pn;
+    const int na = c.na;
+    const int32_t *off = c.off;
+    for (int t0 = 0; t0 < n; t0 += 32) {
+        int k = t0 + lane;
+        bool valid = k < n;
+        int s = valid ? (k < qn ? qsrc[k] : psrc[k - qn]) : 0;
+        const uint64_t *src = srows + row_word(s, 0, Ws);
+        uint64_t cur = 0;
+        int o = 0;
+        for (int wi = 0; wi < na; wi += 4) {
+            uint64_t x[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = (valid && wi + j < na) ? src[c.aw[wi + j] * 32] : 0ULL;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (wi + j >= na) break;
+                const int w = c.aw[wi + j];
+                const uint64_t *m = c.cm + w * 7;
+                CompressMasks cm;
+                cm.m = m[0];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) cm.mv[q] = m[1 + q];
+                uint64_t cw = compress_apply(x[j], cm);
+                int bits = __popcll(cm.m);
+                int b = off[w] & 63;
+                cur |= cw << b;
+                if (b + bits >= 64) {
+                    drows[row_word(k, o, Wd)] = cur;
+                    ++o;
+                    cur = (b + bits > 64) ? (cw >> (64 - b)) : 0;
+                }
+            }
+        }
+        if (o < Wd) drows[row_word(k, o, Wd)] = cur;
+    }
+    __syncwarp();
+}
+
+// Compacts the ids of L selected by L' (lane w holds word w of L') into dst.
+__device__ void compact_ids(Ctx &c, const int32_t *Lid, uint64_t Lw, int W, int32_t *dst)
+{
+    const int32_t *off = c.off;
+    if (c.lane < W) {
+        int pos = off[c.lane];
+        uint64_t b = Lw;
+        while (b) {
+            int t = __ffsll(b) - 1;
+            b &= b - 1;
+            dst[pos++] = Lid[c.lane * 64 + t];
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ uint64_t sum_keys_v(Ctx &c, const int32_t *Lid, uint64_t Lw, int W)
+{
+    uint64_t s = 0;
+    if (c.lane < W) {
+        uint64_t b = Lw;
+        while (b) {
+            int t = __ffsll(b) - 1;
+            b &= b - 1;
+            s += key_v(Lid[c.lane * 64 + t]);
+        }
+    }
+    return warp_sum64(s);
+}
+
+// Appends one biclique to the caller's output buffer: |R|, |L|, R ids, L ids.
+__device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase, int nRbase, int x_id,
+                              const int32_t *rfull, int nfull, const int32_t *Lid, uint64_t Lw, int W, int mL)
+{
+    int nR = nRbase + 1 + nfull;
+    int64_t need = 2 + nR + mL;
+    unsigned long long pos = 0, b = 0;
+    if (c.lane == 0) {
+        pos = atomicAdd(a.used_ids, (unsigned long long)need);
+        b = atomicAdd(a.used_bic, 1ULL);
+    }
+    pos = __shfl_sync(kFull, pos, 0);
+    b = __shfl_sync(kFull, b, 0);
+    if ((int64_t)b >= a.cap_bic || (int64_t)(pos + need) > a.cap_ids) {
+        if (c.lane == 0) set_error(a, MBE_ERR_OUTPUT_FULL);
+        return;
+    }
+    int32_t *o = a.out_ids + pos;
+    if (c.lane == 0) {
+        a.out_offsets[b] = (int64_t)pos;
+        o[0] = nR;
+        o[1] = mL;
+        o[2 + nRbase] = x_id;
+    }
+    for (int k = c.lane; k < nRbase; k += 32) o[2 + k] = Rbase[k];
+    for (int k = c.lane; k < nfull; k += 32) o[3 + nRbase + k] = rfull[k];
+    compact_ids(c, Lid, Lw, W, o + 2 + nR);
+}
+
+// ------------------------------------------------------------ node (frame)
+// One iteration of Algorithm 1's while loop on the top frame at fp: pop
+// x = P[i], build L' = L n N(x) (= row of x), check maximality against the
+// Q-like positions (inherited Q and the P entries popped earlier), expand
+// R' and collect P' from the later positions, emit, and push the child
+// frame when P' is nonempty. Returns the child's address or NULL.
+__device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
+{
+    const int lane = c.lane;
+    Frame F = frame_of(fp);
+    const int W = F.h->W, nQ = F.h->nQ, nP = F.h->nP, n = nQ + nP;
+    const int i = F.h->i;
+    const int kx = nQ + i;
+    __syncwarp(); // every lane has read the header before lane 0 advances the cursor
+    if (lane == 0) F.h->i = i + 1;
+    c.nodes += 1;
+
+    // Step 2: L' = L n N(x) is the row of x (lane w holds word w).
+    uint64_t t_scan = tnow(a);
+    uint64_t Lw = lane < W ? F.rows[row_word(kx, lane, W)] : 0ULL;
+    const int mp = __reduce_add_sync(kFull, (unsigned)__popcll(Lw));
+    set_active_words(c, Lw);
+
+    // Step 3: maximality check over positions [0, kx).
+    Scratch &S = c.s;
+    int qn = 0;
+    bool rejected = false;
+    const int q_end = (kx + 31) >> 5;
+    for (int t0 = 0; t0 < q_end && !rejected; t0 += kTiles) {
+        int cnt[kTiles];
+        count_tiles<kTiles>(c, F.rows, W, t0, q_end, cnt);
+#pragma unroll
+        for (int u = 0; u < kTiles; ++u) {
+            const int k = (t0 + u) * 32 + lane;
+            const bool valid = (t0 + u < q_end) && k < kx;
+            if (__ballot_sync(kFull, valid && cnt[u] == mp)) {
+                rejected = true;
+                break;
+            }
+            const bool part = valid && cnt[u] > 0;
+            const unsigned bal = __ballot_sync(kFull, part);
+            if (part) S.qsrc[qn + __popc(bal & lanemask_lt())] = k;
+            qn += __popc(bal);
+        }
+    }
+    {
+        // algorithmic bytes: x's row, the cheaper of the Q rows and the L'
+        // columns over Q (|Q| = kx here), and the later P rows when maximal
+        const uint64_t nq = (uint64_t)kx, rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
+        c.bytes += 8ULL * ((uint64_t)W + (rows < cols ? rows : cols) + (rejected ? 0ULL : (uint64_t)W * (n - kx - 1)));
+    }
+    if (rejected) {
+        if (lane == 0) tadd(a, c, 1, t_scan);
+        return nullptr;
+    }
+
+    // Step 4: maximal expansion over positions (kx, n).
+    uint64_t rsum = 0;
+    int pn = 0, nfull = 0;
+    const int ntiles = (n + 31) >> 5;
+    for (int t0 = (kx + 1) >> 5; t0 < ntiles; t0 += kTiles) {
+        int cnt[kTiles];
+        count_tiles<kTiles>(c, F.rows, W, t0, ntiles, cnt);
+#pragma unroll
+        for (int u = 0; u < kTiles; ++u) {
+            const int k = (t0 + u) * 32 + lane;
+            const bool valid = (t0 + u < ntiles) && k > kx && k < n;
+            const bool full = valid && cnt[u] == mp;
+            const bool part = valid && cnt[u] > 0 && cnt[u] < mp;
+            const int g = (full || part) ? F.gid[k] : 0;
+            if (full) rsum += key_u(g);
+            if (a.emit) {
+                const unsigned fb = __ballot_sync(kFull, full);
+                if (full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = g;
+                nfull += __popc(fb);
+            }
+            const unsigned bal = __ballot_sync(kFull, part);
+            if (part) {
+                const int p = pn + __popc(bal & lanemask_lt());
+                S.pkey[p] = ((uint64_t)cnt[u] << a.key_shift) | (uint64_t)(uint32_t)g;
+                S.psrc[p] = k;
+            }
+            pn += __popc(bal);
+        }
+    }
+    if (lane == 0) tadd(a, c, 1, t_scan);
+    rsum = warp_sum64(rsum);
+    const int xg = F.gid[kx];
+    const uint64_t Rs = F.h->Rsum + key_u(xg) + rsum;
+    const uint64_t lsum = sum_keys_v(c, F.Lid, Lw, W);
+    c.cnt += 1;
+    c.hash += splitmix(Rs + lsum);
+
+    uint64_t t_build = tnow(a);
+    if (a.emit || pn > 0) prepare_masks(c, Lw, W);
+    if (a.emit) emit_biclique(a, c, F.R, F.h->nR, xg, S.rtmp, nfull, F.Lid, Lw, W, mp);
+    if (pn == 0) {
+        if (lane == 0) tadd(a, c, 2, t_build);
+        return nullptr;
+    }
+
+    // Child frame: [Q' | P' sorted by (count, id)], rows packed to L'.
+    const int Wd = (mp + 63) >> 6;
+    const int nd = qn + pn;
+    const int nRd = a.emit ? F.h->nR + 1 + nfull : 0;
+    const int64_t sz = frame_bytes(mp, nd, Wd, nRd);
+    char *cp = fp + F.h->bytes;
+    if (cp + sz > c.limit) {
+        if (lane == 0) set_error(a, kErrArena);
+        c.abort = true;
+        return nullptr;
+    }
+    int key_bits = a.key_shift + (32 - __clz(mp));
+    warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, pn, key_bits);
+    const uint64_t id_mask = (1ULL << a.key_shift) - 1;
+    Frame D = frame_at(cp, mp, nd, Wd);
+    for (int k = lane; k < qn; k += 32) D.gid[k] = F.gid[S.qsrc[k]];
+    for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
+    compact_ids(c, F.Lid, Lw, W, D.Lid);
+    build_child_rows(c, F.rows, W, S.qsrc, qn, S.psrc, pn, D.rows, Wd);
+    if (a.emit) {
+        int nr0 = F.h->nR;
+        for (int k = lane; k < nr0; k += 32) D.R[k] = F.R[k];
+        if (lane == 0) D.R[nr0] = xg;
+        for (int k = lane; k < nfull; k += 32) D.R[nr0 + 1 + k] = S.rtmp[k];
+    }
+    if (lane == 0) {
+        FrameHdr h;
+        h.m = mp;
+        h.W = Wd;
+        h.nQ = qn;
+        h.nP = pn;
+        h.i = 0;
+        h.end = pn;
+        h.root = F.h->root;
+        h.graph = F.h->graph;
+        h.Rsum = Rs;
+        h.nR = nRd;
+        h.depth = F.h->depth + 1;
+        h.bytes = sz;
+        h.parent = fp - c.arena;
+        *D.h = h;
+        tadd(a, c, 2, t_build);
+    }
+    __syncwarp();
+    return cp;
+}
+
+// ------------------------------------------------------------- root task
+// The top-level iteration for candidate r: L' = N(r), the root-local
+// universe of N2(r), the check against the earlier-ranked candidates, the
+// expansion by the later-ranked ones, and the level-1 frame at the bottom
+// of the stack. Returns true when a frame was pushed.
+__device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r, int graph, int part, int parts)
+{
+    const int lane = c.lane;
+    const uint64_t t_root = tnow(a);
+    const int ro = G.u_off[r];
+    const int d = G.u_off[r + 1] - ro;
+    // a pre-split root: every part rebuilds the root node, part 0 alone
+    // counts it, and part p pops its own contiguous share of P'
+    const bool first = part == 0;
+    if (first) c.nodes += 1;
+    if (d == 0) return false;
+    const int W = (d + 63) >> 6;
+    if (W > a.max_words) {
+        if (lane == 0) set_error(a, kErrUnsupported);
+        c.abort = true;
+        return false;
+    }
+    Scratch &S = c.s;
+    int32_t *mark = c.mark;
+
+    // Discovery: for every (j, w = N(r)[j]) and u in N(w), u != r, give u a
+    // local id and set bit j of its row. Pairs are flattened across up to
+    // 32 consecutive w so that lanes stay busy when degrees are small.
+    int nc = 0, zeroed = 0;
+    uint64_t pairs_total = 0;
+    for (int j0 = 0; j0 < d; j0 += 32) {
+        int j = j0 + lane;
+        bool vj = j < d;
+        int w = vj ? G.u_adj[ro + j] : 0;
+        int wo = vj ? G.v_off[w] : 0;
+        int wd = vj ? G.v_off[w + 1] - wo : 0;
+        int incl = wd;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int total = __shfl_sync(kFull, incl, 31);
+        const int excl = incl - wd;
+        pairs_total += (uint64_t)total;
+        for (int p0 = 0; p0 < total; p0 += 32) {
+            int p = p0 + lane;
+            bool vp = p < total;
+            int s = 0; // last lane whose segment starts at or before p
+#pragma unroll
+            for (int b = 16; b > 0; b >>= 1) {
+                int cand = s + b;
+                int ex = __shfl_sync(kFull, excl, cand & 31);
+                if (cand < 32 && ex <= p) s = cand;
+            }
+            int jj = j0 + s;
+            int ws = __shfl_sync(kFull, wo, s);
+            int es = __shfl_sync(kFull, excl, s);
+            int u = vp ? G.v_adj[ws + (p - es)] : -1;
+            bool take = vp && u != r;
+            int cur = take ? mark[u] : 0;
+            bool need = take && cur < 0;
+            unsigned grp = __match_any_sync(kFull, need ? u : -2 - lane);
+            int leader_lane = __ffs(grp) - 1;
+            bool leader = need && leader_lane == lane;
+            unsigned lb = __ballot_sync(kFull, leader);
+            int newid = nc + __popc(lb & lanemask_lt());
+            int nnew = __popc(lb);
+            if (nc + nnew > S.ncap || (int64_t)((nc + nnew + 31) >> 5) * W * 32 > S.urow_words) {
+                if (lane == 0) set_error(a, kErrArena);
+                c.abort = true;
+                break;
+            }
+            if (leader) {
+                mark[u] = newid;
+                S.ugid[newid] = u;
+            }
+            // zero every tile that gains its first row in this step
+            while (zeroed * 32 < nc + nnew) {
+                uint64_t *tile = S.urows + (int64_t)zeroed * W * 32;
+                for (int q = lane; q < W * 32; q += 32) tile[q] = 0;
+                ++zeroed;
+            }
+            nc += nnew;
+            __syncwarp();
+            int from = __shfl_sync(kFull, newid, leader_lane);
+            int id = need ? from : cur;
+            if (take) atomicOr(reinterpret_cast<unsigned long long *>(&S.urows[row_word(id, jj >> 6, W)]),
+                               1ULL << (jj & 63));
+        }
+        if (c.abort) break;
+    }
+    __syncwarp();
+    // reset the marks for the next root
+    for (int k = lane; k < nc; k += 32) mark[S.ugid[k]] = -1;
+    __syncwarp();
+    if (first) c.bytes += 4ULL * ((uint64_t)d + pairs_total);
+    if (c.abort) return false;
+
+    // L' = N(r): all d bits (lane w holds word w)
+    uint64_t Lw = 0;
+    if (lane < W) Lw = (lane < W - 1 || (d & 63) == 0) ? ~0ULL : ((1ULL << (d & 63)) - 1);
+    set_active_words(c, Lw);
+
+    // Classify: earlier-ranked candidates (degree, id) < (d, r) form Q.
+    uint64_t rsum = 0;
+    int qn = 0, pn = 0, nfull = 0;
+    const int utiles = (nc + 31) >> 5;
+    for (int t0 = 0; t0 < nc; t0 += 32) {
+        int k = t0 + lane;
+        bool valid = k < nc;
+        int cntv[1];
+        count_tiles<1>(c, S.urows, W, t0 >> 5, utiles, cntv);
+        int cnt = cntv[0], u = 0, du = 0;
+        if (valid) {
+            u = S.ugid[k];
+            du = G.u_off[u + 1] - G.u_off[u];
+        }
+        bool ql = valid && (du < d || (du == d && u < r));
+        if (__ballot_sync(kFull, ql && cnt == d)) { // r's node is not maximal
+            if (lane == 0) tadd(a, c, 0, t_root);
+            return false;
+        }
+        bool full = valid && !ql && cnt == d;
+        bool qpart = ql; // cnt > 0 for every discovered candidate
+        bool ppart = valid && !ql && cnt < d;
+        if (full) rsum += key_u(u);
+        if (a.emit) {
+            unsigned fb = __ballot_sync(kFull, full);
+            if (full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
+            nfull += __popc(fb);
+        }
+        unsigned qb = __ballot_sync(kFull, qpart);
+        if (qpart) S.qsrc[qn + __popc(qb & lanemask_lt())] = k;
+        qn += __popc(qb);
+        unsigned pb = __ballot_sync(kFull, ppart);
+        if (ppart) {
+            int p = pn + __popc(pb & lanemask_lt());
+            S.pkey[p] = ((uint64_t)cnt << a.key_shift) | (uint64_t)(uint32_t)u;
+            S.psrc[p] = k;
+        }
+        pn += __popc(pb);
+    }
+    rsum = warp_sum64(rsum);
+    const uint64_t Rs = key_u(r) + rsum;
+    uint64_t ls = 0;
+    for (int j = lane; j < d; j += 32) ls += key_v(G.u_adj[ro + j]);
+    ls = warp_sum64(ls);
+    if (first) {
+        c.cnt += 1;
+        c.hash += splitmix(Rs + ls);
+    }
+
+    prepare_masks(c, Lw, W);
+    if (a.emit && first) {
+        // L' ids are N(r) itself
+        int nR = 1 + nfull;
+        int64_t need = 2 + nR + d;
+        unsigned long long pos = 0, b = 0;
+        if (lane == 0) {
+            pos = atomicAdd(a.used_ids, (unsigned long long)need);
+            b = atomicAdd(a.used_bic, 1ULL);
+        }
+        pos = __shfl_sync(kFull, pos, 0);
+        b = __shfl_sync(kFull, b, 0);
+        if ((int64_t)b < a.cap_bic && (int64_t)(pos + need) <= a.cap_ids) {
+            int32_t *o = a.out_ids + pos;
+            if (lane == 0) {
+                a.out_offsets[b] = (int64_t)pos;
+                o[0] = nR;
+                o[1] = d;
+                o[2] = r;
+            }
+            for (int k = lane; k < nfull; k += 32) o[3 + k] = S.rtmp[k];
+            for (int k = lane; k < d; k += 32) o[2 + nR + k] = G.u_adj[ro + k];
+        } else if (lane == 0) {
+            set_error(a, MBE_ERR_OUTPUT_FULL);
+        }
+    }
+    if (pn == 0) {
+        if (lane == 0) tadd(a, c, 0, t_root);
+        return false;
+    }
+
+    const int nd = qn + pn;
+    const int nRd = a.emit ? 1 + nfull : 0;
+    const int64_t sz = frame_bytes(d, nd, W, nRd);
+    char *cp = c.arena;
+    if (cp + sz > c.limit) {
+        if (lane == 0) set_error(a, kErrArena);
+        c.abort = true;
+        return false;
+    }
+    int key_bits = a.key_shift + (32 - __clz(d));
+    warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, pn, key_bits);
+    const uint64_t id_mask = (1ULL << a.key_shift) - 1;
+    Frame D = frame_at(cp, d, nd, W);
+    for (int k = lane; k < qn; k += 32) D.gid[k] = S.ugid[S.qsrc[k]];
+    for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
+    for (int k = lane; k < d; k += 32) D.Lid[k] = G.u_adj[ro + k];
+    build_child_rows(c, S.urows, W, S.qsrc, qn, S.psrc, pn, D.rows, W);
+    if (a.emit) {
+        if (lane == 0) D.R[0] = r;
+        for (int k = lane; k < nfull; k += 32) D.R[1 + k] = S.rtmp[k];
+    }
+    if (lane == 0) {
+        FrameHdr h;
+        h.m = d;
+        h.W = W;
+        h.nQ = qn;
+        h.nP = pn;
+        h.i = (int32_t)(((int64_t)pn * part) / parts);
+        h.end = (int32_t)(((int64_t)pn * (part + 1)) / parts);
+        h.root = r;
+        h.graph = graph;
+        h.Rsum = Rs;
+        h.nR = nRd;
+        h.depth = 1;
+        h.bytes = sz;
+        h.parent = -1;
+        *D.h = h;
+        tadd(a, c, 0, t_root);
+    }
+    __syncwarp();
+    return true;
+}
+
+// ---------------------------------------------------------------- stealing
+enum : int32_t { kSlotEmpty = 0, kSlotWriting = 1, kSlotFull = 2, kSlotTaken = 3 };
+
+__device__ void warp_copy(char *dst, const char *src, int64_t bytes, int lane, bool from_other_sm)
+{
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    int64_t n = bytes >> 4;
+    int64_t k = lane;
+    for (; k + 96 < n; k += 128) {
+        int4 v0, v1, v2, v3;
+        if (from_other_sm) {
+            v0 = __ldcg(s + k);
+            v1 = __ldcg(s + k + 32);
+            v2 = __ldcg(s + k + 64);
+            v3 = __ldcg(s + k + 96);
+        } else {
+            v0 = s[k];
+            v1 = s[k + 32];
+            v2 = s[k + 64];
+            v3 = s[k + 96];
+        }
+        d[k] = v0;
+        d[k + 32] = v1;
+        d[k + 64] = v2;
+        d[k + 96] = v3;
+    }
+    for (; k < n; k += 32) d[k] = from_other_sm ? __ldcg(s + k) : s[k];
+    __syncwarp();
+}
+
+// If some worker is idle and this worker's slot is free, give away the upper
+// half of the remaining candidates of its shallowest frame that has at least
+// two left: the copy keeps every candidate (earlier positions stay Q-like
+// for the thief), with i = mid; this worker keeps [i, mid).
+__device__ void maybe_donate(const SearchArgs &a, Ctx &c, char *top)
+{
+    const int lane = c.lane;
+    int idle = 0, state = 0;
+    if (lane == 0) {
+        idle = *reinterpret_cast<volatile int32_t *>(a.n_idle) -
+               *reinterpret_cast<volatile int32_t *>(a.n_published);
+        state = *reinterpret_cast<volatile int32_t *>(a.slot_state + c.wid);
+    }
+    idle = __shfl_sync(kFull, idle, 0);
+    state = __shfl_sync(kFull, state, 0);
+    if (idle <= 0 || state != kSlotEmpty) return;
+    // walk frames from the bottom of the stack
+    char *fp = c.arena;
+    while (true) {
+        FrameHdr *h = reinterpret_cast<FrameHdr *>(fp);
+        int left = h->end - h->i;
+        if (left >= 2 && h->bytes <= a.slot_bytes && h->bytes <= a.stack_bytes) {
+            int mid = h->i + (left + 1) / 2;
+            char *slot = a.slots + (int64_t)c.wid * a.slot_bytes;
+            if (lane == 0) {
+                a.slot_state[c.wid] = kSlotWriting;
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), 1ULL);
+            }
+            __syncwarp();
+            uint64_t t_cp = tnow(a);
+            warp_copy(slot, fp, h->bytes, lane, false);
+            if (lane == 0) tadd(a, c, 3, t_cp);
+            if (lane == 0) {
+                FrameHdr *sh = reinterpret_cast<FrameHdr *>(slot);
+                sh->i = mid;
+                sh->parent = -1;
+                h->end = mid;
+                __threadfence();
+                atomicExch(a.slot_state + c.wid, kSlotFull);
+                atomicAdd(a.n_published, 1);
+            }
+            __syncwarp();
+            c.t_don += 1;
+            return;
+        }
+        if (fp == top) return;
+        fp += h->bytes;
+    }
+}
+
+// Claims a published frame: the own slot first, then the others circularly.
+__device__ bool try_steal(const SearchArgs &a, Ctx &c)
+{
+    const int lane = c.lane;
+    int pub = 0;
+    if (lane == 0) pub = *reinterpret_cast<volatile int32_t *>(a.n_published);
+    pub = __shfl_sync(kFull, pub, 0);
+    if (pub <= 0) return false;
+    const int nw = a.n_warps;
+    for (int base = 0; base < nw; base += 32) {
+        int idx = base + lane;
+        int s = (c.wid + idx) % nw;
+        int st = idx < nw ? *reinterpret_cast<volatile int32_t *>(a.slot_state + s) : kSlotEmpty;
+        unsigned cand = __ballot_sync(kFull, st == kSlotFull);
+        while (cand) {
+            int l = __ffs(cand) - 1;
+            cand &= cand - 1;
+            int victim = (c.wid + base + l) % nw;
+            int ok = 0;
+            if (lane == 0) {
+                ok = atomicCAS(a.slot_state + victim, kSlotFull, kSlotTaken) == kSlotFull;
+                if (ok) atomicSub(a.n_published, 1);
+            }
+            ok = __shfl_sync(kFull, ok, 0);
+            if (!ok) continue;
+            __threadfence();
+            const char *slot = a.slots + (int64_t)victim * a.slot_bytes;
+            int64_t bytes = 0;
+            if (lane == 0) bytes = __ldcg(reinterpret_cast<const long long *>(slot + 48));
+            bytes = __shfl_sync(kFull, bytes, 0);
+            if (bytes > a.stack_bytes || bytes > a.slot_bytes || bytes < 64) {
+                // cannot happen for frames published by maybe_donate; refuse rather than overrun
+                if (lane == 0) {
+                    set_error(a, kErrArena);
+                    atomicExch(a.slot_state + victim, kSlotEmpty);
+                }
+                c.abort = true;
+                return false;
+            }
+            uint64_t t_cp = tnow(a);
+            warp_copy(c.arena, slot, bytes, lane, true);
+            if (lane == 0) tadd(a, c, 3, t_cp);
+            __threadfence();
+            if (lane == 0) atomicExch(a.slot_state + victim, kSlotEmpty);
+            __syncwarp();
+            if (victim != c.wid) c.t_steal += 1;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Runs the frames on the stack until it is empty (or the run aborts).
+__device__ void run_stack(const SearchArgs &a, Ctx &c, char *top)
+{
+    const int lane = c.lane;
+    while (top != nullptr && !c.abort) {
+        FrameHdr *h = reinterpret_cast<FrameHdr *>(top);
+        if (h->i >= h->end) {
+            int64_t par = h->parent;
+            top = par < 0 ? nullptr : c.arena + par;
+            c.depth -= 1;
+            continue;
+        }
+        if (++c.since_check >= 16) {
+            c.since_check = 0;
+            int err = 0;
+            if (lane == 0) {
+                err = *reinterpret_cast<volatile int32_t *>(a.error);
+                if (!err && past_deadline(a, c)) {
+                    set_error(a, kErrTimeout);
+                    err = kErrTimeout;
+                }
+            }
+            err = __shfl_sync(kFull, err, 0);
+            trace(a, c, 2, h->depth);
+            if (err) {
+                c.abort = true;
+                break;
+            }
+            if (a.steal) maybe_donate(a, c, top);
+        }
+        char *child = process_node(a, c, top);
+        __syncwarp(); // header updates by lane 0 are visible to the whole warp
+        if (child) {
+            top = child;
+            c.depth += 1;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ void finish_task(const SearchArgs &a, Ctx &c, int owner)
+{
+    if (c.lane == 0) {
+        if (a.per_task_owner && owner >= 0) {
+            unsigned long long *p = a.per_task_owner + 4LL * owner;
+            atomicAdd(p + 0, (unsigned long long)c.cnt);
+            atomicAdd(p + 1, (unsigned long long)c.hash);
+            atomicAdd(p + 2, (unsigned long long)c.nodes);
+            atomicAdd(p + 3, (unsigned long long)c.bytes);
+        }
+        atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), ~0ULL); // -1
+    }
+    c.t_cnt += c.cnt;
+    c.t_hash += c.hash;
+    c.t_nodes += c.nodes;
+    c.t_bytes += c.bytes;
+    c.cnt = c.hash = c.nodes = c.bytes = 0;
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(256, 2) search_rows_kernel(SearchArgs a)
+{
+    extern __shared__ uint32_t smem[];
+    Ctx c;
+    c.lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    c.wid = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (c.wid >= a.n_warps) return;
+    uint32_t *my = smem + wib * kSmemWords;
+    c.hist = my;
+    c.off = reinterpret_cast<int32_t *>(my + 256);
+    c.cm = reinterpret_cast<uint64_t *>(my + 256 + 32);
+    c.lw = reinterpret_cast<uint64_t *>(my + 256 + 32 + 32 * 7 * 2);
+    c.aw = reinterpret_cast<int32_t *>(my + 256 + 32 + 32 * 7 * 2 + 64);
+    c.na = 0;
+    c.dbg = a.debug ? a.debug + (int64_t)MBE_TRACE_WORDS * c.wid : nullptr;
+    c.arena = a.arena + (int64_t)c.wid * a.arena_bytes;
+    c.mark = a.mark + (int64_t)c.wid * a.mark_stride;
+    {
+        // scratch (top of the arena): seven candidate lists of n_cand_cap
+        // entries, then the root universe rows
+        char *q = c.arena + a.arena_bytes - a.scratch_bytes;
+        c.limit = c.arena + a.stack_bytes;
+        const int64_t nc = a.n_cand_cap;
+        c.s.ncap = nc;
+        c.s.qsrc = reinterpret_cast<int32_t *>(q);
+        q += pad16(4 * nc);
+        c.s.psrc = reinterpret_cast<int32_t *>(q);
+        q += pad16(4 * nc);
+        c.s.psrc2 = reinterpret_cast<int32_t *>(q);
+        q += pad16(4 * nc);
+        c.s.rtmp = reinterpret_cast<int32_t *>(q);
+        q += pad16(4 * nc);
+        c.s.ugid = reinterpret_cast<int32_t *>(q);
+        q += pad16(4 * nc);
+        c.s.pkey = reinterpret_cast<uint64_t *>(q);
+        q += 8 * nc;
+        c.s.pkey2 = reinterpret_cast<uint64_t *>(q);
+        q += 8 * nc;
+        c.s.urows = reinterpret_cast<uint64_t *>(q);
+        c.s.urow_words = a.urow_bytes / 8;
+    }
+    c.cnt = c.hash = c.nodes = c.bytes = 0;
+    c.t_cnt = c.t_hash = c.t_nodes = c.t_bytes = c.t_don = c.t_steal = 0;
+    c.since_check = 0;
+    c.abort = false;
+    c.t_start = __shfl_sync(kFull, globaltimer(), 0);
+    c.depth = 0;
+
+    bool idle = false;
+    uint64_t idle_since = 0;
+    unsigned backoff = 64;
+    while (true) {
+        // 1) next root task in execution order
+        long long t = -1;
+        if (c.lane == 0) {
+            if (*reinterpret_cast<volatile int32_t *>(a.error) == 0 &&
+                (long long)*reinterpret_cast<volatile unsigned long long *>(a.cursor) < a.n_tasks) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), 1ULL);
+                t = (long long)atomicAdd(a.cursor, 1ULL);
+                if (t >= a.n_tasks) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), ~0ULL);
+                    t = -1;
+                }
+            }
+        }
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= 0) {
+            if (idle && c.lane == 0) atomicSub(a.n_idle, 1);
+            idle = false;
+            int g = a.task_graph ? a.task_graph[t] : 0;
+            int r = a.task_root[t];
+            int sp = a.task_split ? a.task_split[t] : 0;
+            int parts = sp ? (sp >> 16) : 1, part = sp ? (sp & 0xffff) : 0;
+            GView G = gview(a, g);
+            trace(a, c, 1, r);
+            backoff = 64;
+            uint64_t t_busy = tnow(a);
+            bool pushed = process_root(a, c, G, r, g, part, parts);
+            c.depth = pushed ? 1 : 0;
+            if (pushed && !c.abort) run_stack(a, c, c.arena);
+            if (c.lane == 0) {
+                tadd(a, c, 5, t_busy);
+                if (c.dbg) c.dbg[14] += 1;
+            }
+            finish_task(a, c, a.per_root_mode == 2 ? g : r);
+            if (c.abort) break;
+            continue;
+        }
+        // 2) a published frame (own slot first)
+        if (a.steal && try_steal(a, c)) {
+            if (idle && c.lane == 0) atomicSub(a.n_idle, 1);
+            idle = false;
+            const FrameHdr *h = reinterpret_cast<const FrameHdr *>(c.arena);
+            int owner = a.per_root_mode == 2 ? h->graph : h->root;
+            trace(a, c, 3, owner);
+            backoff = 64;
+            c.depth = 1;
+            uint64_t t_busy = tnow(a);
+            run_stack(a, c, c.arena);
+            if (c.lane == 0) {
+                tadd(a, c, 5, t_busy);
+                if (c.dbg) c.dbg[15] += 1;
+            }
+            finish_task(a, c, owner);
+            if (c.abort) break;
+            continue;
+        }
+        // 3) idle: wait for work or for the end
+        if (!idle) {
+            if (c.lane == 0) atomicAdd(a.n_idle, 1);
+            idle = true;
+            idle_since = __shfl_sync(kFull, globaltimer(), 0);
+        }
+        int done = 0, err = 0;
+        if (c.lane == 0) {
+            long long out = *reinterpret_cast<volatile long long *>(a.outstanding);
+            unsigned long long cur = *reinterpret_cast<volatile unsigned long long *>(a.cursor);
+            done = (out == 0 && (long long)cur >= a.n_tasks);
+            err = *reinterpret_cast<volatile int32_t *>(a.error);
+        }
+        done = __shfl_sync(kFull, done, 0);
+        err = __shfl_sync(kFull, err, 0);
+        if (done || err) {
+            if (c.lane == 0) atomicSub(a.n_idle, 1);
+            break;
+        }
+        // time-based decisions are taken by lane 0 and broadcast: each lane
+        // reads its own timer, and lanes must never leave the loop apart
+        int expired = 0;
+        if (c.lane == 0) expired = (long long)(globaltimer() - idle_since) > a.watchdog_ns || past_deadline(a, c);
+        expired = __shfl_sync(kFull, expired, 0);
+        if (expired) {
+            if (c.lane == 0) {
+                set_error(a, kErrTimeout);
+                atomicSub(a.n_idle, 1);
+            }
+            trace(a, c, 5, 0);
+            break;
+        }
+        trace(a, c, 4, 0);
+        __nanosleep(backoff);
+        if (backoff < 8192) backoff <<= 1;
+    }
+    trace(a, c, 6, c.abort ? 1 : 0);
+    if (c.lane == 0) {
+        atomicAdd(a.totals + 0, (unsigned long long)c.t_cnt);
+        atomicAdd(a.totals + 1, (unsigned long long)c.t_hash);
+        atomicAdd(a.totals + 2, (unsigned long long)c.t_nodes);
+        atomicAdd(a.totals + 3, (unsigned long long)c.t_bytes);
+        atomicAdd(a.totals + 4, (unsigned long long)c.t_don);
+        atomicAdd(a.totals + 5, (unsigned long long)c.t_steal);
+    }
+}
+
+} // namespace
+
+int search_rows_smem_per_warp() { return kSmemWords * 4; }
+
+int search_rows_fit_shape(int threads, int blocks_per_sm_req)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, search_rows_kernel) != cudaSuccess) return 0;
+    if (threads > fa.maxThreadsPerBlock) return -fa.maxThreadsPerBlock / 32 * 32;
+    int smem = (threads / 32) * search_rows_smem_per_warp();
+    // the limit is a property of the kernel shared by every launch: keep it at
+    // the largest block's need (never lower it for a smaller block)
+    cudaFuncSetAttribute(search_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         32 * search_rows_smem_per_warp());
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_rows_kernel, threads, smem) != cudaSuccess)
+        return 0;
+    return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
+}
+
+cudaError_t launch_search_rows(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
+{
+    // the dynamic shared memory limit is raised once to the largest block
+    // (no attribute calls between captured launches)
+    static int smem_set[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int smem = (threads / 32) * search_rows_smem_per_warp();
+    if (dev >= 0 && dev < 64 && smem_set[dev] < 32 * search_rows_smem_per_warp()) {
+        cudaError_t e = cudaFuncSetAttribute(search_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             32 * search_rows_smem_per_warp());
+        if (e != cudaSuccess) return e;
+        smem_set[dev] = 32 * search_rows_smem_per_warp();
+    }
+    search_rows_kernel<<<blocks, threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+} // namespace mbe

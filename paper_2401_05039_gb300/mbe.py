@@ -37,12 +37,13 @@ class Options(ctypes.Structure):
                 ("emit", ctypes.c_int32), ("watchdog_ms", ctypes.c_int32), ("root_begin", ctypes.c_int32),
                 ("root_end", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("model", ctypes.c_void_p),
                 ("per_root", ctypes.c_void_p), ("exec_order", ctypes.c_void_p), ("n_exec", ctypes.c_int32),
-                ("class_params", ctypes.c_void_p)]
+                ("class_params", ctypes.c_void_p), ("layout", ctypes.c_int32)]
 
 
 class ClassParams(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("steal", ctypes.c_int32),
-                ("valid", ctypes.c_int32), ("tuned_ms", ctypes.c_double)]
+                ("valid", ctypes.c_int32), ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tuned_ms", ctypes.c_double)]
 
 
 N_CLASSES = 8

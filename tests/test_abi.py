@@ -58,6 +58,8 @@ int main(void) {{
          offsetof(mbe_options, per_root), offsetof(mbe_options, n_exec));
   printf("%zu %zu %zu\\n", offsetof(mbe_result, device_ms), offsetof(mbe_result, status),
          offsetof(mbe_result, n_donations));
+  printf("%zu %zu %zu %zu\\n", offsetof(mbe_options, layout), sizeof(mbe_class_params),
+         offsetof(mbe_class_params, layout), offsetof(mbe_class_params, tuned_ms));
   return 0;
 }}''')
     exe = tmp_path / "layout"
@@ -68,6 +70,8 @@ int main(void) {{
     assert vals[:3] == [ctypes.sizeof(O), ctypes.sizeof(R), ctypes.sizeof(B)]
     assert vals[3:7] == [O.arena_bytes.offset, O.model.offset, O.per_root.offset, O.n_exec.offset]
     assert vals[7:10] == [R.device_ms.offset, R.status.offset, R.n_donations.offset]
+    C = m.ClassParams
+    assert vals[10:14] == [O.layout.offset, ctypes.sizeof(C), C.layout.offset, C.tuned_ms.offset]
 
 
 def test_compress_helper_matches_bit_gather(tmp_path):

@@ -42,23 +42,26 @@ def _exp(d):
     return (d["count"], int(d["hash"], 16), d["nodes"], d["bytes"])
 
 
-def test_batch_selected_graphs_match_oracle(mbe, gold, graphs):
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_batch_selected_graphs_match_oracle(mbe, gold, graphs, layout):
+    # layout 0 = the automatic choice per class; 1 = rows, 2 = columns
     ids = sorted(int(k) for k in gold["per_graph"])
     b = synth.pack([graphs[i] for i in ids])
-    per, tot = mbe.enumerate_batch(b)
+    per, tot = mbe.enumerate_batch(b, layout=layout)
     assert tot.status == 0
     for k, i in enumerate(ids):
         assert _row(per[k]) == _exp(gold["per_graph"][str(i)]), i
     assert tot.count == sum(int(p.count) for p in per)
 
 
-def test_batch_heavy_graph_roots(mbe, gold, graphs):
+@pytest.mark.parametrize("layout", [1, 2])
+def test_batch_heavy_graph_roots(mbe, gold, graphs, layout):
     import torch
     for gi, rows in gold["heavy_graph_roots"].items():
         g = graphs[int(gi)]
         G = mbe.Graph.from_synth(g)
         buf = torch.zeros((g.nU, 4), dtype=torch.int64, device="cuda")
-        G.enumerate(per_root=buf)
+        G.enumerate(per_root=buf, layout=layout)
         got = buf.cpu().numpy().view(np.uint64)
         G.close()
         for root, d in rows.items():
@@ -79,6 +82,6 @@ def test_batch_equals_single_graph_calls_and_autotune(mbe, gold, graphs):
     table = mbe.autotune_batch(b, sample_per_class=16)
     classes = {mbe.batch_class(g.nU, g.nV, g.nE) for g in sub}
     for c in classes:
-        assert table[c].valid == 1 and table[c].block_threads > 0
+        assert table[c].valid == 1 and table[c].block_threads > 0 and table[c].layout in (1, 2)
     per2, tot2 = mbe.enumerate_batch(b, class_params=table)
     assert [_row(p) for p in per2] == [_row(p) for p in per]

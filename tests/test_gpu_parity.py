@@ -16,6 +16,9 @@ from tests import helpers as H
 
 pytestmark = pytest.mark.gpu
 
+# both search frame layouts (1 = rows, 2 = columns): the result must not depend on the layout
+LAYOUTS = [1, 2]
+
 
 @pytest.fixture(scope="module")
 def mbe():
@@ -43,7 +46,8 @@ def gpu_tuple(r):
     return (int(r.count), int(r.hash), int(r.nodes), int(r.bytes_alg))
 
 
-def test_er200x300_full_set(mbe, golden_dir):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_er200x300_full_set(mbe, golden_dir, layout):
     import torch
     g = synth.workload("er200x300")
     with open(os.path.join(golden_dir, "er200x300.json")) as f:
@@ -52,7 +56,7 @@ def test_er200x300_full_set(mbe, golden_dir):
     c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
     G = mbe.Graph.from_synth(g)
     buf = mbe.Bicliques.allocate(200000, 10000)
-    r = G.enumerate(emit=1, bicliques=buf.buf)
+    r = G.enumerate(emit=1, bicliques=buf.buf, layout=layout)
     torch.cuda.synchronize()
     assert gpu_tuple(r) == (c, h, n, b)
     got = buf.decode()
@@ -76,40 +80,44 @@ def _random_cases(seed, n, max_expected=3000):
 
 
 @pytest.mark.parametrize("seed", range(4))
-def test_random_graphs_vs_oracle(mbe, seed):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_random_graphs_vs_oracle(mbe, seed, layout):
     for g in _random_cases(1000 + seed, 30):
-        assert gpu_tuple(run(mbe, g)) == oracle_tuple(g), (g.nU, g.nV, g.nE)
+        assert gpu_tuple(run(mbe, g, layout=layout)) == oracle_tuple(g), (g.nU, g.nV, g.nE)
 
 
-def test_wide_rows_multiword(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_wide_rows_multiword(mbe, layout):
     # degrees near 90, 315 and 1100 give rows of 2, 5 and 18 words
     rng = np.random.default_rng(7)
     for nU, nV, p in [(16, 200, 0.45), (12, 700, 0.45), (12, 2000, 0.55)]:
         g = H.random_graph(rng, nU, nV, p)
-        assert gpu_tuple(run(mbe, g)) == oracle_tuple(g), (nV, p)
+        assert gpu_tuple(run(mbe, g, layout=layout)) == oracle_tuple(g), (nV, p)
 
 
-def test_closed_forms(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_closed_forms(mbe, layout):
     for a, b in [(1, 1), (3, 200), (70, 5), (40, 130)]:
-        r = run(mbe, H.complete(a, b))
+        r = run(mbe, H.complete(a, b), layout=layout)
         assert r.count == 1 and r.nodes == a
     for n in [1, 33, 100]:
-        assert run(mbe, H.matching(n)).count == n
+        assert run(mbe, H.matching(n), layout=layout).count == n
     for n in [3, 6, 10, 13]:
-        r = run(mbe, H.crown(n))
+        r = run(mbe, H.crown(n), layout=layout)
         assert r.count == 2 ** n - 2
         assert gpu_tuple(r) == oracle_tuple(H.crown(n))
-    r = run(mbe, H.empty(10, 10))
+    r = run(mbe, H.empty(10, 10), layout=layout)
     assert (r.count, r.hash, r.nodes) == (0, 0, 0)
 
 
-def test_emit_matches_closure(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_emit_matches_closure(mbe, layout):
     import torch
     rng = np.random.default_rng(9)
     g = H.random_graph(rng, 60, 140, 0.15)
     G = mbe.Graph.from_synth(g)
     buf = mbe.Bicliques.allocate(500000, 50000)
-    r = G.enumerate(emit=1, bicliques=buf.buf)
+    r = G.enumerate(emit=1, bicliques=buf.buf, layout=layout)
     torch.cuda.synchronize()
     got = buf.decode()
     adj = H.adjacency_sets(g)
@@ -119,16 +127,18 @@ def test_emit_matches_closure(mbe):
     G.close()
 
 
-def test_options_do_not_change_result(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_options_do_not_change_result(mbe, layout):
     g = synth.workload("er200x300")
-    base = gpu_tuple(run(mbe, g))
+    base = gpu_tuple(run(mbe, g, layout=layout))
     assert base == oracle_tuple(g)
     for kw in [dict(steal=0), dict(block_threads=32, blocks_per_sm=1), dict(block_threads=1024, blocks_per_sm=1),
                dict(block_threads=128, blocks_per_sm=4)]:
-        assert gpu_tuple(run(mbe, g, **kw)) == base, kw
+        assert gpu_tuple(run(mbe, g, layout=layout, **kw)) == base, kw
 
 
-def test_explicit_orders_and_shards(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_explicit_orders_and_shards(mbe, layout):
     import torch
     g = synth.workload("er200x300")
     base = oracle_tuple(g)
@@ -136,24 +146,25 @@ def test_explicit_orders_and_shards(mbe):
     rng = np.random.default_rng(3)
     for order in [live, live[::-1].copy(), rng.permutation(live)]:
         t = torch.from_numpy(np.ascontiguousarray(order)).cuda()
-        assert gpu_tuple(run(mbe, g, exec_order=t, n_exec=len(order))) == base
+        assert gpu_tuple(run(mbe, g, exec_order=t, n_exec=len(order), layout=layout)) == base
     # shards of the execution order add up
     G = mbe.Graph.from_synth(g)
     n = len(live)
-    parts = [G.enumerate(root_begin=b, root_end=e) for b, e in [(0, 37), (37, 120), (120, n)]]
+    parts = [G.enumerate(root_begin=b, root_end=e, layout=layout) for b, e in [(0, 37), (37, 120), (120, n)]]
     tot = (sum(p.count for p in parts), sum(p.hash for p in parts) % (1 << 64), sum(p.nodes for p in parts),
            sum(p.bytes_alg for p in parts))
     assert tot == base
     G.close()
 
 
-def test_per_root_matches_oracle(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_per_root_matches_oracle(mbe, layout):
     import torch
     g = synth.workload("er200x300")
     pr = oracle.per_root(g, nthreads=4)
     G = mbe.Graph.from_synth(g)
     buf = torch.zeros((g.nU, 4), dtype=torch.int64, device="cuda")
-    G.enumerate(per_root=buf)
+    G.enumerate(per_root=buf, layout=layout)
     got = buf.cpu().numpy().view(np.uint64)
     assert (got == pr).all()
     G.close()
@@ -181,23 +192,25 @@ def _check_per_root_rows(mbe, g, gold, **kw):
     return r, got
 
 
-def test_planted5k_totals(mbe, golden_dir):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_planted5k_totals(mbe, golden_dir, layout):
     gold = _golden(golden_dir, "planted5k")
     g = synth.workload("planted5k")
     assert g.digest() == gold["graph"]["digest"], "generator drew a different graph on this machine"
-    r, got = _check_per_root_rows(mbe, g, gold)
+    r, got = _check_per_root_rows(mbe, g, gold, layout=layout)
     t = gold["total"]
     assert gpu_tuple(r) == (t["count"], int(t["hash"], 16), t["nodes"], t["bytes"])
     assert int(got[:, 0].sum()) == t["count"]
 
 
-def test_chunglu20k_roots(mbe, golden_dir):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_chunglu20k_roots(mbe, golden_dir, layout):
     # per-root rows of a seeded uniform prefix of the roots (their exact sum
     # and individual rows); the whole-graph total when the oracle finished it
     gold = _golden(golden_dir, "chunglu20k")
     g = synth.workload("chunglu20k")
     assert g.digest() == gold["graph"]["digest"], "generator drew a different graph on this machine"
-    r, got = _check_per_root_rows(mbe, g, gold)
+    r, got = _check_per_root_rows(mbe, g, gold, layout=layout)
     pre = gold["prefix"]
     live = np.nonzero(np.diff(g.u_off) > 0)[0]
     perm = np.random.default_rng(pre["seed"]).permutation(live)[:pre["k"]]
@@ -213,11 +226,12 @@ def test_chunglu20k_roots(mbe, golden_dir):
         assert gpu_tuple(r)[:nb] == (t["count"], int(t["hash"], 16), t["nodes"], t["bytes"])[:nb]
 
 
-def test_chunglu200k_sampled_roots(mbe, golden_dir):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_chunglu200k_sampled_roots(mbe, golden_dir, layout):
     gold = _golden(golden_dir, "chunglu200k")
     g = synth.workload("chunglu200k")
     assert g.digest() == gold["graph"]["digest"]
-    r, got = _check_per_root_rows(mbe, g, gold)
+    r, got = _check_per_root_rows(mbe, g, gold, layout=layout)
     # whole-graph consistency: per-root rows add up to the totals
     assert int(got[:, 0].sum()) == r.count
     assert int(got[:, 2].sum()) == r.nodes
@@ -239,24 +253,26 @@ def test_invalid_graphs_rejected(mbe):
     assert e.value.status == 2
 
 
-def test_arena_overflow_is_reported_then_recovers(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_arena_overflow_is_reported_then_recovers(mbe, layout):
     g = synth.workload("er200x300")
     G = mbe.Graph.from_synth(g)
-    r = G.enumerate(arena_bytes=256, check=False)
+    r = G.enumerate(arena_bytes=256, check=False, layout=layout)
     assert r.status == 4  # MBE_ERR_ARENA_FULL, no hang, no fault
-    r2 = G.enumerate()
+    r2 = G.enumerate(layout=layout)
     assert gpu_tuple(r2) == oracle_tuple(g)
     G.close()
 
 
-def test_watchdog_expires_cleanly(mbe):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_watchdog_expires_cleanly(mbe, layout):
     # one worker holds the single heavy root while the others wait for work;
     # a 1 ms watchdog makes their wait run out: the call returns
     # MBE_ERR_TIMEOUT, and the next call with the default watchdog succeeds
     g = H.crown(18)
     G = mbe.Graph.from_synth(g)
-    r = G.enumerate(watchdog_ms=1, steal=0, check=False)
+    r = G.enumerate(watchdog_ms=1, steal=0, check=False, layout=layout)
     assert r.status == 6
-    r2 = G.enumerate()
+    r2 = G.enumerate(layout=layout)
     assert r2.status == 0 and r2.count == 2 ** 18 - 2
     G.close()
