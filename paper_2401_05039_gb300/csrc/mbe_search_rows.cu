@@ -216,9 +216,9 @@ __device__ __forceinline__ void set_error(const SearchArgs &a, int code)
 // Ascending sort of n (key, value) pairs held in scratch; result in (k0, v0).
 // n <= 32: bitonic network in registers; larger: LSD radix sort, 8-bit
 // digits, stable scatter by warp ranking (match_any + popc).
-__device__ void warp_sort(Ctx &c, uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v1, int n, int key_bits)
+__device__ __forceinline__ void warp_sort_impl(int lane, uint32_t *hist_smem, uint64_t *k0, int32_t *v0, uint64_t *k1,
+                                               int32_t *v1, int n, int key_bits)
 {
-    const int lane = c.lane;
     if (n <= 1) return;
     if (n <= 32) {
         uint64_t key = lane < n ? k0[lane] : ~0ULL;
@@ -247,7 +247,7 @@ __device__ void warp_sort(Ctx &c, uint64_t *k0, int32_t *v0, uint64_t *k1, int32
         return;
     }
     int passes = (key_bits + 7) / 8;
-    uint32_t *hist = c.hist;
+    uint32_t *hist = hist_smem;
     for (int pass = 0; pass < passes; ++pass) {
         int shift = pass * 8;
         for (int b = lane; b < 256; b += 32) hist[b] = 0;
@@ -309,6 +309,12 @@ __device__ void warp_sort(Ctx &c, uint64_t *k0, int32_t *v0, uint64_t *k1, int32
         }
         __syncwarp();
     }
+}
+
+__device__ __forceinline__ void warp_sort(Ctx &c, uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v1, int n,
+                                          int key_bits)
+{
+    warp_sort_impl(c.lane, c.hist, k0, v0, k1, v1, n, key_bits);
 }
 
 // ---------------------------------------------------------------- row scans
