@@ -384,3 +384,43 @@ class Bicliques:
             l = tuple(sorted(ids[o + 2 + nr:o + 2 + nr + nl].tolist()))
             out.append((r, l))
         return out
+
+
+# ------------------------------------------------------------ several ranks
+# Roots are independent units: a graph's execution order can be split into
+# contiguous shards (mbe_options.root_begin / root_end), one per rank, and the
+# shard results add up (count, nodes, bytes as integers, the hash mod 2^64).
+
+def shard_bounds(n: int, rank: int, world: int):
+    """[begin, end) of rank's contiguous share of n roots (sizes differ by at most one)."""
+    if world < 1 or not 0 <= rank < world or n < 0:
+        raise ValueError("need 0 <= rank < world and n >= 0")
+    q, r = divmod(n, world)
+    begin = rank * q + min(rank, r)
+    return begin, begin + q + (1 if rank < r else 0)
+
+
+def allreduce_totals(totals, group=None):
+    """Sum (count, hash, nodes, bytes) over the ranks of a torch.distributed group.
+
+    The values are split into 16-bit limbs in int64 tensors, so the sums are
+    exact for any number of ranks that fits in 2^47, on any backend (gloo on
+    the CPU, NCCL on GPUs); the hash is returned mod 2^64.
+    """
+    import torch
+    import torch.distributed as dist
+    vals = [int(v) & 0xFFFFFFFFFFFFFFFF for v in totals]
+    limbs = torch.tensor([[(v >> (16 * k)) & 0xFFFF for k in range(4)] for v in vals], dtype=torch.int64)
+    if dist.get_backend(group) == "nccl":
+        limbs = limbs.cuda()
+    dist.all_reduce(limbs, op=dist.ReduceOp.SUM, group=group)
+    out = [sum(int(x) << (16 * k) for k, x in enumerate(row)) for row in limbs.cpu().tolist()]
+    out[1] &= 0xFFFFFFFFFFFFFFFF
+    return tuple(out)
+
+
+def sharded_enumerate(graph, rank: int, world: int, n_roots: int, group=None, **kw):
+    """Rank's shard of graph's execution order (n_roots = its length), summed over the group."""
+    b, e = shard_bounds(n_roots, rank, world)
+    r = graph.enumerate(root_begin=b, root_end=e, **kw)
+    return allreduce_totals((r.count, r.hash, r.nodes, r.bytes_alg), group)
