@@ -51,6 +51,8 @@ constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32 + 34 * 2;
 // and a rolled sorting network ran the column kernel 6-12% faster).
 constexpr int kTiles = 4;      // 32-row tiles whose loads a lane keeps in flight together
 constexpr int kUnionLoads = 4; // column words a lane keeps in flight while forming Q'
+constexpr int kGather = 2;    // source words of a child row gathered before compression
+constexpr int kCopyLoads = 1; // words a lane copies per step in q_copy_columns (a rarely taken path)
 // a child's Q' columns are compressed when that leaves at most 1/4 of the words
 constexpr int kCompressNum = 1, kCompressDen = 4;
 // roots whose neighbours' degrees sum to at least this order L by degree class
@@ -431,7 +433,7 @@ __device__ __forceinline__ void prepare_masks(Ctx &c, uint64_t Lw, int W)
 
 // Writes the rows of a child frame: row k' is source row src(k') of the
 // source tile array, compressed to the bits of L' (masks from prepare_masks,
-// active words from set_active_words). Source words are gathered four at a
+// active words from set_active_words). Source words are gathered kGather at a
 // time before they are compressed.
 __device__ void build_child_rows(Ctx &c, const uint64_t *srows, int Ws, const int32_t *psrc, int n,
                                  uint64_t *drows, int Wd)
@@ -446,12 +448,12 @@ __device__ void build_child_rows(Ctx &c, const uint64_t *srows, int Ws, const in
         const uint64_t *src = srows + row_word(s, 0, Ws);
         uint64_t cur = 0;
         int o = 0;
-        for (int wi = 0; wi < na; wi += 4) {
-            uint64_t x[4];
+        for (int wi = 0; wi < na; wi += kGather) {
+            uint64_t x[kGather];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) x[j] = (valid && wi + j < na) ? src[c.aw[wi + j] * 32] : 0ULL;
+            for (int j = 0; j < kGather; ++j) x[j] = (valid && wi + j < na) ? src[c.aw[wi + j] * 32] : 0ULL;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < kGather; ++j) {
                 if (wi + j >= na) break;
                 const int w = c.aw[wi + j];
                 const uint64_t *m = c.cm + w * 7;
@@ -694,11 +696,11 @@ __device__ void q_copy_columns(Ctx &c, const uint64_t *Q, int QW, int LW, uint64
     const int lane = c.lane;
     // mp * QWd words: the frame fits the stack, far below 2^31 words
     const unsigned total = (unsigned)mp * (unsigned)QWd;
-    for (unsigned b = 0; b < total; b += 128) {
-        uint64_t x[4];
-        int64_t di[4];
+    for (unsigned b = 0; b < total; b += 32 * kCopyLoads) {
+        uint64_t x[kCopyLoads];
+        int64_t di[kCopyLoads];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kCopyLoads; ++u) {
             const unsigned idx = b + 32 * u + lane;
             di[u] = -1;
             x[u] = 0;
@@ -713,7 +715,7 @@ __device__ void q_copy_columns(Ctx &c, const uint64_t *Q, int QW, int LW, uint64
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kCopyLoads; ++u)
             if (di[u] >= 0) dst[di[u]] = x[u];
     }
     __syncwarp();
