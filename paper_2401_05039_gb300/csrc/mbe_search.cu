@@ -49,7 +49,7 @@ constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32 + 34 * 2;
 // Loads in flight are balanced against code size: the kernel's hot loop
 // has to stay in the instruction cache (measured: fewer unrolled loads here
 // and a rolled sorting network ran the column kernel 6-12% faster).
-constexpr int kTiles = 4;      // 32-row tiles whose loads a lane keeps in flight together
+constexpr int kTiles = 2;      // 32-row tiles whose loads a lane keeps in flight together
 constexpr int kUnionLoads = 4; // column words a lane keeps in flight while forming Q'
 constexpr int kGather = 2;    // source words of a child row gathered before compression
 constexpr int kCopyLoads = 1; // words a lane copies per step in q_copy_columns (a rarely taken path)
