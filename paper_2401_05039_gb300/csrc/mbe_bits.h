@@ -37,26 +37,44 @@ struct CompressMasks {
     uint64_t mv[6]; // bits that move at stage i (positions before that stage)
 };
 
+// Stage i of the mask preparation: the bits of m that move at this stage.
+MBE_HD uint64_t compress_stage(uint64_t &m, uint64_t &zeros_below, int i)
+{
+    // prefix parity from the right of zeros_below: bit j is the parity of the
+    // count of marked positions at or below j, i.e. bit i of each selected
+    // bit's remaining move distance
+    uint64_t par = zeros_below ^ (zeros_below << 1);
+    par ^= par << 2;
+    par ^= par << 4;
+    par ^= par << 8;
+    par ^= par << 16;
+    par ^= par << 32;
+    const uint64_t move = par & m;
+    m = (m ^ move) | (move >> (1 << i));
+    zeros_below &= ~par;
+    return move;
+}
+
 MBE_HD CompressMasks compress_prepare(uint64_t m)
 {
     CompressMasks c;
     c.m = m;
     uint64_t zeros_below = ~m << 1; // marks positions that have an unselected bit just below them
-    for (int i = 0; i < 6; ++i) {
-        // prefix parity from the right of zeros_below: bit j is the parity of
-        // the count of marked positions at or below j, i.e. bit i of each
-        // selected bit's remaining move distance
-        uint64_t par = zeros_below ^ (zeros_below << 1);
-        par ^= par << 2;
-        par ^= par << 4;
-        par ^= par << 8;
-        par ^= par << 16;
-        par ^= par << 32;
-        uint64_t move = par & m;
-        c.mv[i] = move;
-        m = (m ^ move) | (move >> (1 << i));
-        zeros_below &= ~par;
-    }
+    for (int i = 0; i < 6; ++i) c.mv[i] = compress_stage(m, zeros_below, i);
+    return c;
+}
+
+// The same masks with the six stages kept as a loop on the device (smaller
+// code, for kernels whose hot loop must stay in the instruction cache).
+MBE_HD CompressMasks compress_prepare_rolled(uint64_t m)
+{
+    CompressMasks c;
+    c.m = m;
+    uint64_t zeros_below = ~m << 1;
+#if defined(__CUDA_ARCH__)
+#pragma unroll 1
+#endif
+    for (int i = 0; i < 6; ++i) c.mv[i] = compress_stage(m, zeros_below, i);
     return c;
 }
 

@@ -416,7 +416,7 @@ __device__ __forceinline__ void prepare_offsets(Ctx &c, uint64_t Lw, int W)
 __device__ __forceinline__ void prepare_cm(Ctx &c, uint64_t Lw, int W)
 {
     if (c.lane < W) {
-        CompressMasks cm = compress_prepare(Lw);
+        CompressMasks cm = compress_prepare_rolled(Lw);
         uint64_t *dst = c.cm + c.lane * 7;
         dst[0] = Lw;
 #pragma unroll
@@ -677,7 +677,7 @@ __device__ void q_compress_masks(Ctx &c, int LW)
         }
         if (v) {
             S.offq[w] = run + incl - pc;
-            CompressMasks cm = compress_prepare(m);
+            CompressMasks cm = compress_prepare_rolled(m);
 #pragma unroll
             for (int i = 0; i < 6; ++i) S.cmq[6 * (int64_t)w + i] = cm.mv[i];
         }

@@ -83,7 +83,7 @@ def test_compress_helper_matches_bit_gather(tmp_path):
 #include <random>
 static uint64_t gather(uint64_t x, uint64_t m){uint64_t r=0;int k=0;for(int i=0;i<64;i++) if(m>>i&1){r|=((x>>i)&1ULL)<<k;k++;}return r;}
 int main(){std::mt19937_64 g(5);long bad=0;for(int t=0;t<300000;t++){uint64_t m=g(),x=g();if(t%%3==1)m&=g();if(t%%3==2)m|=g();
- if(t%%97==0)m=0;if(t%%89==0)m=~0ULL;mbe::CompressMasks c=mbe::compress_prepare(m);if(mbe::compress_apply(x,c)!=gather(x,m))bad++;}
+ if(t%%97==0)m=0;if(t%%89==0)m=~0ULL;mbe::CompressMasks c=mbe::compress_prepare(m);if(mbe::compress_apply(x,c)!=gather(x,m))bad++;mbe::CompressMasks c2=mbe::compress_prepare_rolled(m);if(mbe::compress_apply(x,c2)!=gather(x,m))bad++;}
  printf("%%ld\\n",bad);return 0;}''' % os.path.join(ROOT, "paper_2401_05039_gb300", "csrc", "mbe_bits.h"))
     exe = tmp_path / "comp"
     subprocess.check_call(["g++", "-O2", "-std=c++17", str(src), "-o", str(exe)])
