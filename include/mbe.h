@@ -87,12 +87,13 @@ int mbe_graph_info(const mbe_graph *g, int32_t *nU, int32_t *nV, int64_t *nE, in
  * MBE_DEBUG_TRACE set, every search launch keeps a progress record per
  * worker: [0] phase, [1] argument, [2] nodes, [3] depth, [4] donations,
  * [5] steals, [6] elapsed ns, [8..13] ns in root setup, node scans, child
- * builds, frame copies, sorting, tasks; [14] root tasks, [15] stolen tasks,
- * [16..21] child builds: sum of |Q'|, sum of |P'|, builds, sum of |L'|, sum
- * of parent row words, sum of parent candidates; [22] ns in the check
- * against Q, [23] ns building child columns, of which [24] forming Q',
- * [25] copying or compressing the parent's columns, [26] transposing P';
- * [27] child builds that copied the columns uncompressed. This copies up to
+ * builds, frame copies, sorting, tasks; [14] root tasks, [15] stolen tasks;
+ * column layout only: [16..21] child builds: sum of |Q'|, sum of |P'|,
+ * builds, sum of |L'|, sum of parent row words, sum of parent candidates;
+ * [22] ns in the check against Q, [23] ns building child columns, of which
+ * [24] forming Q', [25] copying or compressing the parent's columns, [26]
+ * transposing P'; [27] child builds that copied the columns uncompressed.
+ * The timers read the global timer and slow the search. This copies up to
  * max_workers of them (MBE_TRACE_WORDS uint64 each) to `host` and
  * returns how many were copied. MBE_DEADLINE_MS bounds any single launch
  * (default 30 minutes); a launch past it stops with MBE_ERR_TIMEOUT.

@@ -237,6 +237,15 @@ def test_chunglu200k_sampled_roots(mbe, golden_dir, layout):
     assert int(got[:, 2].sum()) == r.nodes
 
 
+def test_invalid_layout_rejected(mbe):
+    g = synth.workload("er200x300")
+    G = mbe.Graph.from_synth(g)
+    for bad in (-1, 3):
+        assert G.enumerate(layout=bad, check=False).status == 1  # MBE_ERR_INVALID_ARG
+    assert gpu_tuple(G.enumerate(layout=0)) == oracle_tuple(g)
+    G.close()
+
+
 def test_invalid_graphs_rejected(mbe):
     g = H.random_graph(np.random.default_rng(1), 10, 12, 0.4)
     bad = g.u_adj.copy()
