@@ -477,39 +477,24 @@ __device__ void build_child_rows(Ctx &c, const uint64_t *srows, int Ws, const in
     __syncwarp();
 }
 
-// Compacts the ids of L selected by L' (lane w holds word w of L') into dst.
-__device__ void compact_ids(Ctx &c, const int32_t *Lid, uint64_t Lw, int W, int32_t *dst)
+// Compacts the ids of L at the positions J[0..m) (the bits of L') into dst.
+__device__ __forceinline__ void compact_ids(Ctx &c, const int32_t *Lid, const int32_t *J, int m, int32_t *dst)
 {
-    const int32_t *off = c.off;
-    if (c.lane < W) {
-        int pos = off[c.lane];
-        uint64_t b = Lw;
-        while (b) {
-            int t = __ffsll(b) - 1;
-            b &= b - 1;
-            dst[pos++] = Lid[c.lane * 64 + t];
-        }
-    }
+    for (int t = c.lane; t < m; t += 32) dst[t] = Lid[J[t]];
     __syncwarp();
 }
 
-__device__ __forceinline__ uint64_t sum_keys_v(Ctx &c, const int32_t *Lid, uint64_t Lw, int W)
+// Sum of key_v over the ids of L at the positions J[0..m).
+__device__ __forceinline__ uint64_t sum_keys_v(Ctx &c, const int32_t *Lid, const int32_t *J, int m)
 {
     uint64_t s = 0;
-    if (c.lane < W) {
-        uint64_t b = Lw;
-        while (b) {
-            int t = __ffsll(b) - 1;
-            b &= b - 1;
-            s += key_v(Lid[c.lane * 64 + t]);
-        }
-    }
+    for (int t = c.lane; t < m; t += 32) s += key_v(Lid[J[t]]);
     return warp_sum64(s);
 }
 
 // Appends one biclique to the caller's output buffer: |R|, |L|, R ids, L ids.
 __device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase, int nRbase, int x_id,
-                              const int32_t *rfull, int nfull, const int32_t *Lid, uint64_t Lw, int W, int mL)
+                              const int32_t *rfull, int nfull, const int32_t *Lid, const int32_t *J, int mL)
 {
     int nR = nRbase + 1 + nfull;
     int64_t need = 2 + nR + mL;
@@ -533,22 +518,62 @@ __device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase,
     }
     for (int k = c.lane; k < nRbase; k += 32) o[2 + k] = Rbase[k];
     for (int k = c.lane; k < nfull; k += 32) o[3 + nRbase + k] = rfull[k];
-    compact_ids(c, Lid, Lw, W, o + 2 + nR);
+    compact_ids(c, Lid, J, mL, o + 2 + nR);
 }
 
 // ---------------------------------------------------------------- Q columns
-// Positions (in L) of the bits of L', ascending (lane w holds word w of L';
-// offsets from prepare_masks).
-__device__ __forceinline__ void bit_positions(Ctx &c, uint64_t Lw, int W, int32_t *dst)
+// Position (0..63) of the r-th set bit (r < popcount(x)) of x: a binary
+// search over halves, quarters, ... with popcounts (six steps, no loop).
+__device__ __forceinline__ int select_bit(uint64_t x, int r)
 {
-    if (c.lane < W) {
-        int pos = c.off[c.lane];
-        uint64_t b = Lw;
-        while (b) {
-            int t = __ffsll(b) - 1;
-            b &= b - 1;
-            dst[pos++] = c.lane * 64 + t;
+    int pos = 0;
+    int n = __popc((uint32_t)x);
+    if (r >= n) { r -= n; x >>= 32; pos += 32; }
+    n = __popc((uint32_t)x & 0xffffu);
+    if (r >= n) { r -= n; x >>= 16; pos += 16; }
+    n = __popc((uint32_t)x & 0xffu);
+    if (r >= n) { r -= n; x >>= 8; pos += 8; }
+    n = __popc((uint32_t)x & 0xfu);
+    if (r >= n) { r -= n; x >>= 4; pos += 4; }
+    n = __popc((uint32_t)x & 0x3u);
+    if (r >= n) { r -= n; x >>= 2; pos += 2; }
+    if (r >= (int)(x & 1u)) pos += 1;
+    return pos;
+}
+
+// Positions (in L) of the mp bits of L', ascending (lane w holds word w of
+// L'): lane t finds the t-th one directly (its active word by a binary
+// search over the word offsets of prepare_offsets, then the bit by
+// select_bit), so no lane walks many bits one by one. Needs
+// set_active_words and prepare_offsets.
+// An L' of at most kSerialBits bits is listed by each word's lane walking its
+// bits (cheaper for a few bits); a longer one by the direct selection.
+constexpr int kSerialBits = 8;
+
+__device__ __forceinline__ void bit_positions(Ctx &c, uint64_t Lw, int W, int mp, int32_t *dst)
+{
+    if (mp <= kSerialBits) {
+        if (c.lane < W) {
+            int pos = c.off[c.lane];
+            uint64_t b = Lw;
+            while (b) {
+                int t = __ffsll(b) - 1;
+                b &= b - 1;
+                dst[pos++] = c.lane * 64 + t;
+            }
         }
+        __syncwarp();
+        return;
+    }
+    for (int t = c.lane; t < mp; t += 32) {
+        int lo = 0, hi = c.na - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (c.off[c.aw[mid]] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        const int w = c.aw[lo];
+        dst[t] = w * 64 + select_bit(c.lw[lo], t - c.off[w]);
     }
     __syncwarp();
 }
@@ -883,7 +908,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     prepare_offsets(c, Lw, W);
     Scratch &S = c.s;
     int32_t *J = S.jlist;
-    bit_positions(c, Lw, W, J);
+    bit_positions(c, Lw, W, mp, J);
 
     // Step 3: maximality check against Algorithm 1's Q at this iteration:
     // the inherited Q and the P entries popped before x, i.e. the first
@@ -938,12 +963,12 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     rsum = warp_sum64(rsum);
     const int xg = F.gid[i];
     const uint64_t Rs = F.h->Rsum + key_u(xg) + rsum;
-    const uint64_t lsum = sum_keys_v(c, F.Lid, Lw, W);
+    const uint64_t lsum = sum_keys_v(c, F.Lid, J, mp);
     c.cnt += 1;
     c.hash += splitmix(Rs + lsum);
 
     uint64_t t_build = tnow(a);
-    if (a.emit) emit_biclique(a, c, F.R, F.h->nR, xg, S.rtmp, nfull, F.Lid, Lw, W, mp);
+    if (a.emit) emit_biclique(a, c, F.R, F.h->nR, xg, S.rtmp, nfull, F.Lid, J, mp);
     if (pn > 0) prepare_cm(c, Lw, W);
     if (pn == 0) {
         if (lane == 0) tadd(a, c, 2, t_build);
@@ -1009,7 +1034,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
     Frame D = frame_at(cp, mp, QWd, pn, Wd);
     for (int k = lane; k < pn; k += 32) D.gid[k] = (int32_t)(S.pkey[k] & id_mask);
-    compact_ids(c, F.Lid, Lw, W, D.Lid);
+    compact_ids(c, F.Lid, J, mp, D.Lid);
     build_child_rows(c, F.rows, W, S.psrc, pn, D.rows, Wd);
     t_qc = tnow(a);
     if (compress) {
