@@ -6,7 +6,7 @@ touches the GPU library. Usage:
     python oracle/make_golden.py er200x300 planted5k chunglu20k chunglu200k batch4096 [--threads N]
 
 Each workload writes ``tests/golden/<name>.json`` with the graph digest (so a
-machine that draws a different graph is caught before parity is judged),
+machine that draws a different graph is caught before parity is checked),
 oracle totals where the oracle can finish the whole graph, and per-root
 (count, hash, nodes, bytes) rows for a sample of roots. Hashes are written
 as hex strings.

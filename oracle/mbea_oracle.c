@@ -3,7 +3,7 @@
  *
  * TEST INFRASTRUCTURE ONLY. Nothing in the library's product path may call
  * this code: it exists so that tests, the smoke check and the benchmark's
- * CPU-baseline leg can judge the GPU path. It shares no source with the GPU
+ * CPU-baseline leg can check the GPU path. It shares no source with the GPU
  * path.
  *
  * What it computes (paper Section II-A, problem definition): for a bipartite

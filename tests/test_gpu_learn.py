@@ -107,7 +107,7 @@ def test_learned_schedule_same_results_and_better_order(mbe):
     r2, pr2 = G.per_root(schedule=2, model=model)
     assert _tuple(r0) == _tuple(r1) == _tuple(r2)
     assert (pr0 == pr1).all() and (pr0 == pr2).all()
-    # the learned order ranks roots by predicted cost; judged by the measured subtree nodes
+    # the learned order ranks roots by predicted cost; checked against the measured subtree nodes
     f = G.features()
     pred = model.predict(f).cpu().numpy()
     live = np.nonzero(np.diff(g.u_off) > 0)[0]
