@@ -246,6 +246,18 @@ def test_invalid_layout_rejected(mbe):
     G.close()
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_root_degree_beyond_bitset_limit_is_unsupported(mbe, layout):
+    # a root with more than 2,048 neighbours (32 words per bitset row) is
+    # outside the bitset path: the call reports MBE_ERR_UNSUPPORTED cleanly
+    # and the next call on another graph is unaffected
+    g = H.complete(2, 2100)
+    r = run(mbe, g, layout=layout, check=False)
+    assert r.status == 8
+    g2 = synth.workload("er200x300")
+    assert gpu_tuple(run(mbe, g2, layout=layout)) == oracle_tuple(g2)
+
+
 def test_invalid_graphs_rejected(mbe):
     g = H.random_graph(np.random.default_rng(1), 10, 12, 0.4)
     bad = g.u_adj.copy()
