@@ -170,7 +170,9 @@ typedef struct {
     int32_t steal;            /* 1 = busy workers split their shallowest frame for idle ones (Sec. III-C) */
     int32_t schedule;         /* 0 = static execution order (descending degree); 1 = learned: roots by
                                  descending predicted cost, predicted-heavy roots split into up to 32
-                                 tasks; 2 = learned order without splitting (needs `model`) */
+                                 tasks when steal = 0 (with steal = 1 idle workers split frames
+                                 instead, and nothing is pre-split); 2 = learned order without
+                                 splitting (needs `model`) */
     int32_t emit;             /* 0 = count + hash only, 1 = also write the bicliques */
     int32_t watchdog_ms;      /* bound on any device wait; 0 = 60000 */
     int32_t root_begin;       /* shard of the execution order: positions [root_begin, root_end) */

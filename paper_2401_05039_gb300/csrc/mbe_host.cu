@@ -375,11 +375,15 @@ int root_features(mbe_graph *g, float *d_feat, int32_t *d_raw, cudaStream_t s)
 // The learned execution order: predicted log cost per root, roots by
 // descending prediction (counting sort on quantised keys), and the
 // predicted-heaviest roots split into contiguous shares of their level-1
-// frames (a root predicted above half a worker's fair share of the total is
-// split into up to kMaxParts tasks). Falls back to the static order when a
-// prediction is not finite.
-int learned_schedule(mbe_graph *g, const mbe_model *md, bool presplit, cudaStream_t s, int64_t *n_tasks,
-                     bool *fallback, double *prep_ms)
+// frames. Without work stealing the split is the only balance: a root
+// predicted above half a worker's fair share of the total becomes up to
+// kMaxParts tasks. With stealing, idle workers split heavy frames anyway
+// and every extra part rebuilds its root (measured: splitting even the few
+// heaviest roots into 4 parts cost 10% on the 20k Chung-Lu graph), so
+// nothing is pre-split. Falls back to the static order when a prediction is
+// not finite.
+int learned_schedule(mbe_graph *g, const mbe_model *md, bool presplit, bool stealing, cudaStream_t s,
+                     int64_t *n_tasks, bool *fallback, double *prep_ms)
 {
     const int nU = g->nU;
     cudaEvent_t e0, e1;
@@ -446,7 +450,8 @@ int learned_schedule(mbe_graph *g, const mbe_model *md, bool presplit, cudaStrea
                 const int r = top[k];
                 const double pn = std::expm1((double)pred[r]);
                 int parts = 1;
-                if (share > 0 && pn > 0.5 * share) parts = (int)std::min<double>(kMaxParts, std::ceil(pn / (0.5 * share)));
+                if (!stealing && share > 0 && pn > 0.5 * share)
+                    parts = (int)std::min<double>(kMaxParts, std::ceil(pn / (0.5 * share)));
                 for (int p = 0; p < parts; ++p) {
                     hr.push_back(r);
                     hs.push_back(parts > 1 ? (parts << 16) | p : 0);
@@ -696,7 +701,7 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
         if (!o.model) return set_status(out, MBE_ERR_INVALID_ARG);
         int64_t n_tasks = 0;
         bool fallback = false;
-        int st = learned_schedule(g, static_cast<const mbe_model *>(o.model), o.schedule == 1, s, &n_tasks,
+        int st = learned_schedule(g, static_cast<const mbe_model *>(o.model), o.schedule == 1, o.steal != 0, s, &n_tasks,
                                   &fallback, &prep_ms);
         if (st != MBE_OK) return set_status(out, st);
         if (!fallback) {

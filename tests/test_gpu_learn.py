@@ -105,8 +105,10 @@ def test_learned_schedule_same_results_and_better_order(mbe):
     r0, pr0 = G.per_root()
     r1, pr1 = G.per_root(schedule=1, model=model)
     r2, pr2 = G.per_root(schedule=2, model=model)
-    assert _tuple(r0) == _tuple(r1) == _tuple(r2)
-    assert (pr0 == pr1).all() and (pr0 == pr2).all()
+    # without stealing, schedule 1 pre-splits the predicted-heaviest roots into parts
+    r3, pr3 = G.per_root(schedule=1, model=model, steal=0)
+    assert _tuple(r0) == _tuple(r1) == _tuple(r2) == _tuple(r3)
+    assert (pr0 == pr1).all() and (pr0 == pr2).all() and (pr0 == pr3).all()
     # the learned order ranks roots by predicted cost; checked against the measured subtree nodes
     f = G.features()
     pred = model.predict(f).cpu().numpy()
