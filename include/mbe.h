@@ -118,8 +118,9 @@ int mbe_copy_bandwidth(int64_t bytes, int32_t iters, void *stream, double *gbps)
  * The learned schedule (no counterpart in the paper; it feeds Section III-C's
  * task distribution). A small network predicts log(1 + nodes of a root's
  * subtree) from eight per-root features; mbe_enumerate with schedule = 1
- * runs the roots heaviest-predicted first and splits the heaviest into
- * several tasks. Counts, hashes and nodes never depend on it.
+ * runs the roots heaviest-predicted first and, without work stealing, splits
+ * the heaviest into several tasks. Counts, hashes and nodes never depend on
+ * it.
  */
 typedef struct mbe_model mbe_model;
 
@@ -234,6 +235,8 @@ typedef struct {
  * out receives count, hash, nodes and timings; bicliques may be NULL
  * (count + hash only). The result is independent of every option except
  * root_begin/root_end (which select a shard of roots; shards add up).
+ * Limit: a root with more than 64 * bitset_max_words (at most 2,048)
+ * neighbours returns MBE_ERR_UNSUPPORTED (the launch stops cleanly).
  */
 int mbe_enumerate(const mbe_graph *g, const mbe_options *opts, void *stream, mbe_result *out,
                   mbe_biclique_buffer *bicliques);
@@ -298,7 +301,7 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
  * synchronises the device). Such a caller passes its graph in its own
  * DEVICE arrays (same layout and rules as mbe_graph_create) and receives
  * count, hash, nodes and bytes_alg in the host struct *out (device_ms is -1:
- * the call creates no timing events).
+ * the call creates no timing events). The search runs in the column layout.
  *
  * Scratch: every call uses one fixed 64 MiB array compiled into the
  * library (it exists on every GPU that loads the library until the process
