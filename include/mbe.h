@@ -45,8 +45,9 @@ typedef enum {
     MBE_ERR_INVALID_GRAPH = 2, /* unsorted or duplicate adjacency, id out of range, CSR/CSC not transposes */
     MBE_ERR_OOM = 3,           /* device allocation failed */
     MBE_ERR_ARENA_FULL = 4,    /* a search stack outgrew its arena even after the automatic retries */
-    MBE_ERR_OUTPUT_FULL = 5,   /* biclique buffer too small; count/hash are still exact and the
-                                  required sizes are reported in the buffer's n_*_written fields */
+    MBE_ERR_OUTPUT_FULL = 5,   /* biclique buffer too small: the search still ran to the end, count,
+                                  hash, nodes and bytes_alg are exact and the sizes the output needs
+                                  are reported in the buffer's n_*_written fields */
     MBE_ERR_TIMEOUT = 6,       /* a device wait exceeded options.watchdog_ms; the kernel stopped cleanly */
     MBE_ERR_CUDA = 7,          /* a CUDA runtime call failed (no device, launch failure, ...) */
     MBE_ERR_UNSUPPORTED = 8,   /* input outside the limits stated at the entry point */
@@ -67,8 +68,11 @@ typedef struct mbe_graph mbe_graph; /* opaque, immutable after create */
  * v_adj[nE] the CSR of V -> U; every list strictly increasing, the two forms
  * transposes of each other, u_off[0] = v_off[0] = 0, u_off[nU] = v_off[nV]
  * = nE. ptr_kind = 0: the arrays are host memory; 1: device memory of the
- * current device. The arrays are copied; the caller keeps them. The input
- * is validated on the device; violations return MBE_ERR_INVALID_GRAPH.
+ * current device. The arrays are copied; the caller keeps them. Host input
+ * is checked on the host before anything is copied (offsets, id ranges,
+ * order); then both forms are checked on the device (order, transposes),
+ * by kernels that never index with an unchecked value. Violations return
+ * MBE_ERR_INVALID_GRAPH.
  * Limits: 0 <= nU, nV; 0 <= nE < 2^31.
  */
 int mbe_graph_create(int32_t nU, int32_t nV, int64_t nE, const int32_t *u_off, const int32_t *u_adj,
@@ -214,19 +218,26 @@ typedef struct {
 } mbe_result;
 
 /*
- * Caller-owned DEVICE buffers for the bicliques themselves (emit = 1).
- * Biclique b is ids[offsets[b] .. ]: |R|, |L|, then R's ids, then L's ids
- * (global ids, each side in ascending order after mbe_enumerate returns
- * only if the caller sorts them; the library writes them in search order).
- * Bicliques appear in any order.
+ * Caller-owned DEVICE buffers for the bicliques themselves (emit = 1; the
+ * emit step of Algorithm 1). Biclique b is the record at ids[offsets[b]]:
+ * |R|, |L|, then R's ids in ascending order, then L's ids in ascending
+ * order (ids of the caller's U and V). Records appear in any order.
+ *
+ * On return n_ids_written and n_bicliques_written hold the sizes the whole
+ * output needs (sum over bicliques of 2 + |R| + |L|, and the number of
+ * bicliques), also when they exceed the capacities. If the output does not
+ * fit, mbe_enumerate returns MBE_ERR_OUTPUT_FULL after a complete search:
+ * count, hash, nodes and bytes_alg are exact, the buffers hold an
+ * unspecified subset of the records (do not read them), and a second call
+ * with capacities of at least the reported sizes returns every record.
  */
 typedef struct {
     int32_t *ids;
     int64_t capacity_ids;
     int64_t *offsets;
     int64_t capacity_bicliques;
-    int64_t n_ids_written;       /* out: ids needed (written if <= capacity) */
-    int64_t n_bicliques_written; /* out: bicliques found */
+    int64_t n_ids_written;       /* out: ids the whole output needs (written when <= capacity_ids) */
+    int64_t n_bicliques_written; /* out: bicliques found (records written when they all fit) */
 } mbe_biclique_buffer;
 
 /*
@@ -311,7 +322,11 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
  * first call on a device looks up the array's device address; make that
  * first call before any stream capture. All calls on a device share the
  * array: calls that overlap on the GPU race, so issue them one at a time.
- * Returns an mbe_status like every entry point.
+ * The graph is validated first (MBE_ERR_INVALID_GRAPH), and nothing else
+ * reads the arrays before that verdict is back on the host. The call
+ * synchronises `stream` before it returns. Its device waits are bounded by
+ * fixed limits (60 s for an idle worker, 30 minutes for the search), as the
+ * defaults of mbe_enumerate. Returns an mbe_status like every entry point.
  */
 int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const int32_t *u_off, const int32_t *u_adj,
                           const int32_t *v_off, const int32_t *v_adj, void *stream, mbe_result *out);

@@ -49,9 +49,9 @@ def _load():
             lib.orc_sm.argtypes = [ctypes.c_uint64]
             lib.orc_sm.restype = ctypes.c_uint64
             lib.orc_enumerate.argtypes = [ctypes.c_int32, ctypes.c_int32, _I32P, _I32P, _I32P, _I32P, _U64P,
-                                          ctypes.POINTER(_I32P), _I64P]
+                                          ctypes.POINTER(_I32P), _I64P, _U64P]
             lib.orc_per_root.argtypes = [ctypes.c_int32, ctypes.c_int32, _I32P, _I32P, _I32P, _I32P, _I32P,
-                                         ctypes.c_int64, _U64P, ctypes.c_int32]
+                                         ctypes.c_int64, _U64P, ctypes.c_int32, _U64P]
             lib.orc_root_order.argtypes = [ctypes.c_int32, _I32P, _I32P, _I64P]
             lib.orc_batch.argtypes = [ctypes.c_int32, _I32P, _I32P, _I64P, _I64P, _I64P, _I32P, _I32P, _I32P,
                                       _I32P, _I32P, _U64P, ctypes.c_int32]
@@ -99,42 +99,53 @@ def _arrays(g):
     return _c32(g.u_off), _c32(g.u_adj), _c32(g.v_off), _c32(g.v_adj)
 
 
-def enumerate_graph(g, records: bool = False):
+def enumerate_graph(g, records: bool = False, bytes_b: bool = False):
     """Serial MBEA over the whole graph.
 
     Returns ``(count, hash, nodes, bytes)`` or, with ``records=True``,
     ``(count, hash, nodes, bytes, [(R, L), ...])`` with R, L sorted id tuples.
-    ``bytes`` is the algorithmic byte count of the run.
+    ``bytes`` is the algorithmic byte count of the run; ``bytes_b=True``
+    appends the count under the second byte model (bitset rows or reverse-
+    scanned lists, whichever is cheaper per node).
     """
     lib = _load()
     uo, ua, vo, va = _arrays(g)
     out = np.zeros(4, dtype=np.uint64)
+    ob = np.zeros(1, dtype=np.uint64)
     rec_p, rec_n = _I32P(), ctypes.c_int64(0)
     rc = lib.orc_enumerate(g.nU, g.nV, _p32(uo), _p32(ua), _p32(vo), _p32(va), out.ctypes.data_as(_U64P),
-                           ctypes.byref(rec_p) if records else None, ctypes.byref(rec_n) if records else None)
+                           ctypes.byref(rec_p) if records else None, ctypes.byref(rec_n) if records else None,
+                           ob.ctypes.data_as(_U64P))
     if rc:
         raise MemoryError("oracle enumeration failed")
     res = tuple(int(x) for x in out)
+    if bytes_b:
+        res = res + (int(ob[0]),)
     if records:
         return res + (_records(rec_p, rec_n),)
     return res
 
 
-def per_root(g, roots=None, nthreads: int = 1) -> np.ndarray:
+def per_root(g, roots=None, nthreads: int = 1, bytes_b: bool = False):
     """(count, hash, nodes, bytes) per top-level candidate; uint64 array [len(roots), 4].
 
-    ``roots`` defaults to every U vertex (row u = vertex u).
+    ``roots`` defaults to every U vertex (row u = vertex u). With
+    ``bytes_b=True`` the rows have a fifth column: bytes under the second
+    byte model.
     """
     lib = _load()
     uo, ua, vo, va = _arrays(g)
     roots = np.arange(g.nU, dtype=np.int32) if roots is None else _c32(roots)
     out = np.zeros((roots.shape[0], 4), dtype=np.uint64)
+    ob = np.zeros(max(roots.shape[0], 1), dtype=np.uint64)
     if roots.shape[0] == 0:
-        return out
+        return np.zeros((0, 5), dtype=np.uint64) if bytes_b else out
     rc = lib.orc_per_root(g.nU, g.nV, _p32(uo), _p32(ua), _p32(vo), _p32(va), _p32(roots), roots.shape[0],
-                          out.ctypes.data_as(_U64P), nthreads)
+                          out.ctypes.data_as(_U64P), nthreads, ob.ctypes.data_as(_U64P))
     if rc:
         raise MemoryError("oracle per-root run failed")
+    if bytes_b:
+        return np.concatenate([out, ob[:roots.shape[0], None]], axis=1)
     return out
 
 

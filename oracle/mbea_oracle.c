@@ -151,6 +151,9 @@ typedef struct {
     uint64_t bytes; /* algorithmic bytes, see bytes_node / bytes_root */
     ovec *records;  /* optional: per biclique |R|, |L|, R sorted, L sorted */
     int err;
+    uint64_t bytes_b;      /* the second byte model, see bytes_node_b */
+    const int32_t *rootL;  /* L of the current root's level-1 call, N(r), sorted */
+    int64_t nRootL;
 } oacc;
 
 /*
@@ -171,6 +174,26 @@ static uint64_t bytes_node(int64_t nL, int64_t nLp, int64_t nQ, int64_t n_rest, 
     const uint64_t rows = W * (uint64_t)nQ;
     const uint64_t cols = (uint64_t)nLp * (uint64_t)((nQ + 63) / 64);
     return 8ULL * (W + (rows < cols ? rows : cols) + (maximal ? W * (uint64_t)n_rest : 0));
+}
+
+/*
+ * Second algorithmic-byte model: per node below the top level, the cheaper
+ * of two ways to read what the node needs.
+ *  - Bitset rows: one row of ceil(|L|/32) 32-bit words for x and for every
+ *    other candidate of the call (Q at this pop and P after it).
+ *  - Sorted lists, scanned in reverse (Section III-D): x's adjacency inside
+ *    the root's universe, |N(x) n N(r)| ids, then for every w in L' the ids
+ *    of its neighbours among the other candidates, |N(w) n (Q u P_rest)|.
+ * cx_sum is sum over w in L' of |N(w) n X|, X = Q u P at the call's entry;
+ * at every pop X = Q u P_rest u {x}, and x is adjacent to all of L', so the
+ * second sum is cx_sum - |L'|. All sizes in int32 (4 bytes).
+ */
+static uint64_t bytes_node_b(int64_t nL, int64_t nLp, int64_t nQ, int64_t n_rest, int64_t x_in_root,
+                             uint64_t cx_sum)
+{
+    const uint64_t bits = 4ULL * (uint64_t)((nL + 31) / 32) * (uint64_t)(1 + nQ + n_rest);
+    const uint64_t list = 4ULL * ((uint64_t)x_in_root + cx_sum - (uint64_t)nLp);
+    return bits < list ? bits : list;
 }
 
 static void emit(oacc *acc, const ovec *L, const ovec *R)
@@ -202,10 +225,12 @@ static void mbea(const ograph *g, const ovec *L, const ovec *R, const ovec *P, c
 
 /*
  * One iteration of Algorithm 1's while loop with candidate x already popped:
- * P_rest is P after the pop, Q the current maximality-checking set.
+ * P_rest is P after the pop, Q the current maximality-checking set. cx[k]
+ * (below the top level; NULL there) is |N(L[k]) n X| for the call's
+ * candidate set X (second byte model only).
  */
 static void mbea_iteration(const ograph *g, const ovec *L, const ovec *R, int32_t x, const int32_t *P_rest,
-                           int64_t n_rest, const int32_t *Q, int64_t nQ, oacc *acc)
+                           int64_t n_rest, const int32_t *Q, int64_t nQ, const int64_t *cx, oacc *acc)
 {
     ovec Rp = {0}, Lp = {0}, Pp = {0}, Qp = {0};
     int64_t dx;
@@ -247,14 +272,27 @@ static void mbea_iteration(const ograph *g, const ovec *L, const ovec *R, int32_
             }
         }
         emit(acc, &Lp, &Rp);
+        if (R->n == 0) { /* x is this root: its level-1 call works inside N(x) */
+            acc->rootL = Lp.a;
+            acc->nRootL = Lp.n;
+        }
         if (Pp.n != 0) mbea(g, &Lp, &Rp, &Pp, &Qp, acc);
     }
-    if (R->n == 0) { /* top level: the root's adjacency */
+    if (R->n == 0) { /* top level: the root's adjacency (both byte models) */
         uint64_t b = 4ULL * (uint64_t)dx;
         for (int64_t k = 0; k < dx; ++k) b += 4ULL * (uint64_t)(g->v_off[Nx[k] + 1] - g->v_off[Nx[k]]);
         acc->bytes += b;
+        acc->bytes_b += b;
     } else {
         acc->bytes += bytes_node(L->n, Lp.n, nQ, n_rest, is_maximal);
+        /* sum of cx over L' = L n N(x): both sorted, walk them together */
+        uint64_t cx_sum = 0;
+        for (int64_t i = 0, j = 0; i < L->n && j < Lp.n; ++i)
+            if (L->a[i] == Lp.a[j]) {
+                cx_sum += (uint64_t)cx[i];
+                ++j;
+            }
+        acc->bytes_b += bytes_node_b(L->n, Lp.n, nQ, n_rest, count_common(Nx, dx, acc->rootL, acc->nRootL), cx_sum);
     }
     goto done;
 oom:
@@ -284,8 +322,23 @@ static void mbea(const ograph *g, const ovec *L, const ovec *R, const ovec *P, c
     int64_t nP = P->n;
     okey *ord = (okey *)malloc((size_t)(nP ? nP : 1) * sizeof(okey));
     int32_t *seq = (int32_t *)malloc((size_t)(nP ? nP : 1) * sizeof(int32_t));
+    int32_t *xs = NULL;
+    int64_t *cx = NULL;
     ovec Qc = {0};
     if (!ord || !seq) goto oom;
+    if (R->n > 0) {
+        /* second byte model: cx[k] = |N(L[k]) n X| with X = Q u P, sorted copy */
+        xs = (int32_t *)malloc((size_t)(Q->n + nP ? Q->n + nP : 1) * sizeof(int32_t));
+        cx = (int64_t *)malloc((size_t)(L->n ? L->n : 1) * sizeof(int64_t));
+        if (!xs || !cx) goto oom;
+        memcpy(xs, Q->a, (size_t)Q->n * sizeof(int32_t));
+        memcpy(xs + Q->n, P->a, (size_t)nP * sizeof(int32_t));
+        qsort(xs, (size_t)(Q->n + nP), sizeof(int32_t), cmp_i32);
+        for (int64_t k = 0; k < L->n; ++k) {
+            const int32_t w = L->a[k];
+            cx[k] = count_common(g->v_adj + g->v_off[w], g->v_off[w + 1] - g->v_off[w], xs, Q->n + nP);
+        }
+    }
     /* candidate selection key |N(v) n L|, then id */
     for (int64_t i = 0; i < nP; ++i) {
         int64_t dv;
@@ -300,7 +353,7 @@ static void mbea(const ograph *g, const ovec *L, const ovec *R, const ovec *P, c
 
     for (int64_t i = 0; i < nP && !acc->err; ++i) { /* while |P| > 0 */
         int32_t x = seq[i];                         /* x = P.pop() */
-        mbea_iteration(g, L, R, x, seq + i + 1, nP - i - 1, Qc.a, Qc.n, acc);
+        mbea_iteration(g, L, R, x, seq + i + 1, nP - i - 1, Qc.a, Qc.n, cx, acc);
         if (ov_push(&Qc, x)) goto oom; /* Q = Q u {x} */
     }
     goto done;
@@ -309,6 +362,8 @@ oom:
 done:
     free(ord);
     free(seq);
+    free(xs);
+    free(cx);
     ov_free(&Qc);
 }
 
@@ -323,17 +378,17 @@ static int top_level(const ograph *g, ovec *L, ovec *P)
 }
 
 /*
- * Whole-graph enumeration, serial. out[0..3] = count, hash, nodes, bytes.
- * When rec != NULL, *rec receives a malloc'd int32 array of records
+ * Whole-graph enumeration, serial. out[0..3] = count, hash, nodes, bytes;
+ * *out_b (when not NULL) = bytes under the second model. When rec != NULL, *rec receives a malloc'd int32 array of records
  * (|R|, |L|, R..., L...) and *rec_len its length (free with orc_free).
  * Returns 0, or -1 on allocation failure.
  */
 int orc_enumerate(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
-                  const int32_t *v_adj, uint64_t *out, int32_t **rec, int64_t *rec_len)
+                  const int32_t *v_adj, uint64_t *out, int32_t **rec, int64_t *rec_len, uint64_t *out_b)
 {
     ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
     ovec L = {0}, R = {0}, P = {0}, Q = {0}, records = {0};
-    oacc acc = {0, 0, 0, 0, rec ? &records : NULL, 0};
+    oacc acc = {0, 0, 0, 0, rec ? &records : NULL, 0, 0, NULL, 0};
     if (top_level(&g, &L, &P)) acc.err = 1;
     else mbea(&g, &L, &R, &P, &Q, &acc);
     ov_free(&L);
@@ -342,6 +397,7 @@ int orc_enumerate(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u
     out[1] = acc.hash;
     out[2] = acc.nodes;
     out[3] = acc.bytes;
+    if (out_b) *out_b = acc.bytes_b;
     if (rec) {
         *rec = records.a;
         *rec_len = records.n;
@@ -370,6 +426,7 @@ typedef struct {
     const int32_t *roots;
     int64_t nroots;
     uint64_t *out;
+    uint64_t *out_b;
     int64_t next;
     pthread_mutex_t mu;
     int err;
@@ -380,15 +437,17 @@ static void run_root(root_job *j, int64_t k)
     int32_t r = j->roots[k];
     uint64_t *o = j->out + 4 * k;
     o[0] = o[1] = o[2] = o[3] = 0;
+    if (j->out_b) j->out_b[k] = 0;
     if (r < 0 || r >= j->g->nU || j->pos[r] < 0) return; /* isolated: never popped */
     int64_t i = j->pos[r];
     ovec R = {0};
-    oacc acc = {0, 0, 0, 0, NULL, 0};
-    mbea_iteration(j->g, j->L, &R, r, j->seq + i + 1, j->nseq - i - 1, j->seq, i, &acc);
+    oacc acc = {0, 0, 0, 0, NULL, 0, 0, NULL, 0};
+    mbea_iteration(j->g, j->L, &R, r, j->seq + i + 1, j->nseq - i - 1, j->seq, i, NULL, &acc);
     o[0] = acc.count;
     o[1] = acc.hash;
     o[2] = acc.nodes;
     o[3] = acc.bytes;
+    if (j->out_b) j->out_b[k] = acc.bytes_b;
     if (acc.err) j->err = 1;
 }
 
@@ -407,11 +466,13 @@ static void *root_worker(void *arg)
 
 /*
  * Per-root results: out[4k..4k+3] = (count, hash, nodes, bytes) of the top-level
- * iteration whose candidate is roots[k] (zeros for an isolated vertex).
+ * iteration whose candidate is roots[k] (zeros for an isolated vertex), and
+ * out_b[k] (when out_b is not NULL) its bytes under the second model.
  * Runs on nthreads POSIX threads. Returns 0 or -1.
  */
 int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
-                 const int32_t *v_adj, const int32_t *roots, int64_t nroots, uint64_t *out, int32_t nthreads)
+                 const int32_t *v_adj, const int32_t *roots, int64_t nroots, uint64_t *out, int32_t nthreads,
+                 uint64_t *out_b)
 {
     ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
     ovec L = {0}, P = {0};
@@ -446,6 +507,7 @@ int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_
     job.roots = roots;
     job.nroots = nroots;
     job.out = out;
+    job.out_b = out_b;
     job.next = 0;
     job.err = 0;
     pthread_mutex_init(&job.mu, NULL);
@@ -520,7 +582,7 @@ static void *batch_worker(void *arg)
         const int32_t *uo = j->u_off + j->u_off_start[gi];
         const int32_t *vo = j->v_off + j->v_off_start[gi];
         if (orc_enumerate(j->nU[gi], j->nV[gi], uo, j->u_adj + e0, vo, j->v_adj + e0, j->out + 4 * (int64_t)gi,
-                          NULL, NULL))
+                          NULL, NULL, NULL))
             j->err = 1;
     }
     return NULL;

@@ -75,6 +75,18 @@ int upload(const HostBatch &b, DeviceBatch &d, cudaStream_t s)
     }
     if (nE > 0 && (!b.u_adj_cat || !b.v_adj_cat)) return MBE_ERR_INVALID_ARG;
     if (nE >= ((int64_t)1 << 31)) return MBE_ERR_UNSUPPORTED;
+    if (b.edge_off[0] < 0) return MBE_ERR_INVALID_ARG;
+    // the arrays are host memory: check every graph's offsets and ids here,
+    // so that the device checks below (sortedness, transposes) and every
+    // later kernel index only with values that stay inside the graph
+    for (int32_t i = 0; i < G; ++i) {
+        const int64_t ne = b.edge_off[i + 1] - b.edge_off[i];
+        if (!host_csr_ok(b.u_off_cat + b.u_off_start[i], b.u_adj_cat ? b.u_adj_cat + b.edge_off[i] : nullptr,
+                         b.nU[i], b.nV[i], ne) ||
+            !host_csr_ok(b.v_off_cat + b.v_off_start[i], b.v_adj_cat ? b.v_adj_cat + b.edge_off[i] : nullptr,
+                         b.nV[i], b.nU[i], ne))
+            return MBE_ERR_INVALID_GRAPH;
+    }
     const size_t eb = sizeof(int32_t) * (size_t)std::max<int64_t>(nE, 1);
     d.n_tasks_cap = std::max<int64_t>(n_tasks, 1);
     if (cudaMalloc(&d.uo, sizeof(int32_t) * (size_t)n_uoff) != cudaSuccess ||

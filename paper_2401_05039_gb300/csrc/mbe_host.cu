@@ -168,7 +168,9 @@ cudaError_t launch_layout(const SearchArgs &a, int blocks, const LaunchShape &sh
 int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t frame_max, int32_t max_nU,
                      const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor)
 {
-    const int64_t ncap = std::max<int64_t>(nc_max, 32);
+    // one entry more than the largest candidate set: a new R' list holds the
+    // candidates that join R' and the popped vertex itself
+    const int64_t ncap = std::max<int64_t>(nc_max + 1, 32);
     const int64_t urow = round_up(std::max<int64_t>(urow_max, 256), 256);
     const int64_t scratch = scratch_layout_bytes(ncap, urow);
     int64_t stack = stack_bytes_req > 0 ? stack_bytes_req : (int64_t)stack_factor * frame_max + (256 << 10);
@@ -299,6 +301,7 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
             a.cap_bic = bic->capacity_bicliques;
             a.used_ids = &ws.ctl->used_ids;
             a.used_bic = &ws.ctl->used_bic;
+            a.out_full = &ws.ctl->out_full;
         }
         cudaEvent_t e0, e1;
         MBE_TRY(cudaEventCreate(&e0));
@@ -331,12 +334,31 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
             out->n_workers = a.n_warps;
         }
         if (a.emit) {
+            // sizes the whole output needs (the counters run past the capacities)
             bic->n_ids_written = (int64_t)h.used_ids;
             bic->n_bicliques_written = (int64_t)h.used_bic;
         }
+        if (h.error == 0 && h.out_full) return MBE_ERR_OUTPUT_FULL;
         return h.error;
     }
     return MBE_ERR_ARENA_FULL;
+}
+
+bool host_csr_ok(const int32_t *off, const int32_t *adj, int32_t n, int32_t n_other, int64_t nE)
+{
+    if (n < 0 || nE < 0 || !off || off[0] != 0 || (int64_t)off[n] != nE) return false;
+    if (nE > 0 && !adj) return false;
+    for (int32_t i = 0; i < n; ++i) {
+        const int64_t a = off[i], b = off[i + 1];
+        if (b < a || b > nE) return false;
+        int32_t prev = -1;
+        for (int64_t k = a; k < b; ++k) {
+            const int32_t x = adj[k];
+            if (x <= prev || x >= n_other) return false;
+            prev = x;
+        }
+    }
+    return true;
 }
 
 // Root features of g into d_feat (and d_raw), using the shared workspace's
@@ -543,6 +565,9 @@ int mbe_graph_create(int32_t nU, int32_t nV, int64_t nE, const int32_t *u_off, c
     if (nU < 0 || nV < 0 || nE < 0 || nE >= ((int64_t)1 << 31) || (ptr_kind != 0 && ptr_kind != 1))
         return MBE_ERR_INVALID_ARG;
     if (!u_off || !v_off || (nE > 0 && (!u_adj || !v_adj))) return MBE_ERR_INVALID_ARG;
+    // host input is range-checked before anything reaches the device
+    if (ptr_kind == 0 && (!host_csr_ok(u_off, u_adj, nU, nV, nE) || !host_csr_ok(v_off, v_adj, nV, nU, nE)))
+        return MBE_ERR_INVALID_GRAPH;
     cudaStream_t s = (cudaStream_t)stream;
     mbe_graph *g = new mbe_graph();
     g->nU = nU;

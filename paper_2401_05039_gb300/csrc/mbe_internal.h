@@ -65,8 +65,9 @@ struct SearchArgs {
     int64_t cap_ids;
     int64_t *out_offsets;
     int64_t cap_bic;
-    unsigned long long *used_ids;
-    unsigned long long *used_bic;
+    unsigned long long *used_ids; // ids needed so far (keeps counting past cap_ids)
+    unsigned long long *used_bic; // records needed so far (keeps counting past cap_bic)
+    int32_t *out_full;            // set to 1 when a record did not fit (the search goes on)
 };
 
 // Status codes the kernel writes into *error.

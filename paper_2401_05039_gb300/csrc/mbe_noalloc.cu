@@ -73,7 +73,8 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return fail(status_of(cudaErrorInvalidDevice));
 
-    // Set-up, once per device, with that device current.
+    // Set-up, once per device, with that device current. Two host threads
+    // that race here both store the same address, so the race is benign.
     if (!g_noalloc_ptr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -84,19 +85,24 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     NoAllocCtl *ctl = reinterpret_cast<NoAllocCtl *>(base);
     size_t used = align256(sizeof(NoAllocCtl));
 
-    // Validation and per-root bounds (clears what must start at zero first).
+    // Validation (clears what must start at zero first). Its verdict is read
+    // back before anything else touches the caller's arrays: the bounds
+    // kernel below indexes with the graph's offsets and ids.
     GraphDesc desc{0, 0, 0, nU, nV};
     cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(NoAllocCtl), s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl->desc, &desc, sizeof(desc), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = validate_graph(u_off, u_adj, v_off, v_adj, nU, nV, nE, &ctl->bad, s);
-    if (e == cudaSuccess && nU > 0) e = root_bounds(&ctl->desc, 1, nU, u_off, u_adj, v_off, ctl->bounds, s);
     int32_t bad = 0;
-    unsigned long long hb[8] = {0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, &ctl->bad, sizeof(bad), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, ctl->bounds, sizeof(hb), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return fail(status_of(e));
     if (bad) return fail(MBE_ERR_INVALID_GRAPH);
+    // Per-root workspace bounds of the validated graph.
+    unsigned long long hb[8] = {0};
+    if (nU > 0) e = root_bounds(&ctl->desc, 1, nU, u_off, u_adj, v_off, ctl->bounds, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hb, ctl->bounds, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(status_of(e));
     const int64_t nc_max = (int64_t)hb[0], urow_max = (int64_t)hb[1], frame_max = (int64_t)hb[2];
     const int32_t max_deg = (int32_t)hb[3], n_live = (int32_t)hb[4];
     if (nU == 0 || n_live == 0) return fail(MBE_OK);
@@ -106,7 +112,7 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     used += align256(sizeof(int32_t) * (size_t)nU);
     int32_t *hist = reinterpret_cast<int32_t *>(base + used);
     used += align256(sizeof(int32_t) * (size_t)(max_deg + 1));
-    const int64_t ncap = std::max<int64_t>(nc_max, 32);
+    const int64_t ncap = std::max<int64_t>(nc_max + 1, 32);
     const int64_t urow = (int64_t)align256((size_t)std::max<int64_t>(urow_max, 256));
     const int64_t scratch = scratch_layout_bytes(ncap, urow);
     const int64_t slot = (int64_t)align256((size_t)std::max<int64_t>(frame_max, 4096));

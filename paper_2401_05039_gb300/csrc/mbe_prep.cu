@@ -40,20 +40,38 @@ __global__ void validate_csr_kernel(const int32_t *off, const int32_t *adj, int3
 
 // Every (u, v) of the U-side CSR appears in N(v) of the V-side CSR. With
 // both forms duplicate-free and of equal size, this makes them transposes.
+// It runs on the same stream right after the CSR checks, before anyone has
+// read their verdict, so it trusts nothing: an offset outside [0, nE] or
+// out of order, or an id outside its side, is reported and never used as an
+// index.
 __global__ void validate_transpose_kernel(const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
-                                          const int32_t *v_adj, int32_t nU, int32_t *bad)
+                                          const int32_t *v_adj, int32_t nU, int32_t nV, int64_t nE, int32_t *bad)
 {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < nU; u += stride) {
-        for (int k = u_off[u]; k < u_off[u + 1]; ++k) {
-            int v = u_adj[k];
-            int lo = v_off[v], hi = v_off[v + 1];
+        const int a = u_off[u], b = u_off[u + 1];
+        if (a < 0 || b < a || (int64_t)b > nE) {
+            atomicOr(bad, 4);
+            continue;
+        }
+        for (int k = a; k < b; ++k) {
+            const int v = u_adj[k];
+            if (v < 0 || v >= nV) {
+                atomicOr(bad, 8);
+                break;
+            }
+            const int vlo = v_off[v], vhi = v_off[v + 1];
+            if (vlo < 0 || vhi < vlo || (int64_t)vhi > nE) {
+                atomicOr(bad, 4);
+                break;
+            }
+            int lo = vlo, hi = vhi;
             while (lo < hi) {
                 int mid = lo + ((hi - lo) >> 1);
                 if (v_adj[mid] < u) lo = mid + 1;
                 else hi = mid;
             }
-            if (lo >= v_off[v + 1] || v_adj[lo] != (int32_t)u) {
+            if (lo >= vhi || v_adj[lo] != (int32_t)u) {
                 atomicOr(bad, 16);
                 break;
             }
@@ -289,7 +307,7 @@ cudaError_t validate_graph(const int32_t *u_off, const int32_t *u_adj, const int
     int blocks = 2 * 152, threads = 256;
     validate_csr_kernel<<<blocks, threads, 0, s>>>(u_off, u_adj, nU, nV, nE, d_bad);
     validate_csr_kernel<<<blocks, threads, 0, s>>>(v_off, v_adj, nV, nU, nE, d_bad);
-    validate_transpose_kernel<<<blocks, threads, 0, s>>>(u_off, u_adj, v_off, v_adj, nU, d_bad);
+    validate_transpose_kernel<<<blocks, threads, 0, s>>>(u_off, u_adj, v_off, v_adj, nU, nV, nE, d_bad);
     return cudaGetLastError();
 }
 

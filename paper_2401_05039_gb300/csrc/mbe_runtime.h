@@ -15,7 +15,7 @@ struct Ctl {
     int32_t n_idle;
     int32_t error;
     int32_t n_published;
-    int32_t pad;
+    int32_t out_full; // a biclique record did not fit in the caller's buffer
     unsigned long long totals[8];
     unsigned long long used_ids;
     unsigned long long used_bic;
@@ -87,5 +87,11 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
                      const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor);
 int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStream_t s, mbe_result *out,
                mbe_biclique_buffer *bic);
+
+// Host-side check of one adjacency form held in HOST memory: off[0] = 0,
+// off[n] = nE, offsets non-decreasing, every list strictly increasing with
+// ids in [0, n_other). Run before such arrays are copied to the device, so
+// that no device kernel ever indexes with an unchecked value.
+bool host_csr_ok(const int32_t *off, const int32_t *adj, int32_t n, int32_t n_other, int64_t nE);
 
 } // namespace mbe

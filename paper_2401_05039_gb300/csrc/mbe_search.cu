@@ -37,6 +37,7 @@
 // its frame is pushed, which is the order in which Algorithm 1 pops it
 // because the counts are fixed while L' is fixed.
 #include "mbe_bits.h"
+#include "mbe_emit.cuh"
 #include "mbe_internal.h"
 
 namespace mbe {
@@ -492,32 +493,24 @@ __device__ __forceinline__ uint64_t sum_keys_v(Ctx &c, const int32_t *Lid, const
     return warp_sum64(s);
 }
 
-// Appends one biclique to the caller's output buffer: |R|, |L|, R ids, L ids.
-__device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase, int nRbase, int x_id,
-                              const int32_t *rfull, int nfull, const int32_t *Lid, const int32_t *J, int mL)
+// Appends one biclique to the caller's output buffer: |R|, |L|, R ids, L ids,
+// each side ascending. R' is the merge of the frame's R (ascending) with
+// B[0..nB) (x and the candidates that joined R', sorted); L' is the ids of
+// L at the positions J (ascending ids: L is kept in id order when emitting).
+__device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase, int nRbase, const int32_t *B,
+                              int nB, const int32_t *Lid, const int32_t *J, int mL)
 {
-    int nR = nRbase + 1 + nfull;
-    int64_t need = 2 + nR + mL;
-    unsigned long long pos = 0, b = 0;
-    if (c.lane == 0) {
-        pos = atomicAdd(a.used_ids, (unsigned long long)need);
-        b = atomicAdd(a.used_bic, 1ULL);
-    }
-    pos = __shfl_sync(kFull, pos, 0);
-    b = __shfl_sync(kFull, b, 0);
-    if ((int64_t)b >= a.cap_bic || (int64_t)(pos + need) > a.cap_ids) {
-        if (c.lane == 0) set_error(a, MBE_ERR_OUTPUT_FULL);
-        return;
-    }
+    const int nR = nRbase + nB;
+    int64_t rec = 0;
+    const int64_t pos = emit::reserve(a, c.lane, 2 + (int64_t)nR + mL, &rec);
+    if (pos < 0) return;
     int32_t *o = a.out_ids + pos;
     if (c.lane == 0) {
-        a.out_offsets[b] = (int64_t)pos;
+        a.out_offsets[rec] = pos;
         o[0] = nR;
         o[1] = mL;
-        o[2 + nRbase] = x_id;
     }
-    for (int k = c.lane; k < nRbase; k += 32) o[2 + k] = Rbase[k];
-    for (int k = c.lane; k < nfull; k += 32) o[3 + nRbase + k] = rfull[k];
+    emit::merge_into(c.lane, Rbase, nRbase, B, nB, o + 2);
     compact_ids(c, Lid, J, mL, o + 2 + nR);
 }
 
@@ -968,7 +961,13 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     c.hash += splitmix(Rs + lsum);
 
     uint64_t t_build = tnow(a);
-    if (a.emit) emit_biclique(a, c, F.R, F.h->nR, xg, S.rtmp, nfull, F.Lid, J, mp);
+    if (a.emit) {
+        // B = {x} and the candidates that joined R', ascending
+        if (lane == 0) S.rtmp[nfull] = xg;
+        __syncwarp();
+        emit::sort_ids(lane, c.hist, S.rtmp, S.psrc2, nfull + 1, a.key_shift);
+        emit_biclique(a, c, F.R, F.h->nR, S.rtmp, nfull + 1, F.Lid, J, mp);
+    }
     if (pn > 0) prepare_cm(c, Lw, W);
     if (pn == 0) {
         if (lane == 0) tadd(a, c, 2, t_build);
@@ -1052,12 +1051,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         c.dbg[26] += now - t_tr;
         c.dbg[27] += compress ? 0 : 1;
     }
-    if (a.emit) {
-        int nr0 = F.h->nR;
-        for (int k = lane; k < nr0; k += 32) D.R[k] = F.R[k];
-        if (lane == 0) D.R[nr0] = xg;
-        for (int k = lane; k < nfull; k += 32) D.R[nr0 + 1 + k] = S.rtmp[k];
-    }
+    if (a.emit) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
     if (lane == 0) {
         FrameHdr h;
         h.m = mp;
@@ -1114,8 +1108,10 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     // empties early. Any order of L is valid (L is a set); it is applied
     // only when the root's candidate lists can be long (sum of the degrees
     // of N(r) at least kDegSortMin), and needs room in the lists.
+    // (Not when the bicliques are written: they list L in id order, which the
+    // level sets then keep.)
     const int32_t *Ln = G.u_adj + ro;
-    if (d > 1 && d <= S.ncap) {
+    if (!a.emit && d > 1 && d <= S.ncap) {
         int64_t sdeg = 0;
         for (int j = lane; j < d; j += 32) {
             const int w = G.u_adj[ro + j];
@@ -1263,29 +1259,26 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     }
 
     prepare_masks(c, Lw, W);
-    if (a.emit && first) {
-        // L' ids are N(r) itself
-        int nR = 1 + nfull;
-        int64_t need = 2 + nR + d;
-        unsigned long long pos = 0, b = 0;
-        if (lane == 0) {
-            pos = atomicAdd(a.used_ids, (unsigned long long)need);
-            b = atomicAdd(a.used_bic, 1ULL);
-        }
-        pos = __shfl_sync(kFull, pos, 0);
-        b = __shfl_sync(kFull, b, 0);
-        if ((int64_t)b < a.cap_bic && (int64_t)(pos + need) <= a.cap_ids) {
-            int32_t *o = a.out_ids + pos;
-            if (lane == 0) {
-                a.out_offsets[b] = (int64_t)pos;
-                o[0] = nR;
-                o[1] = d;
-                o[2] = r;
+    if (a.emit) {
+        // R' = {r} and the candidates that joined it, ascending; L' = N(r)
+        if (lane == 0) S.rtmp[nfull] = r;
+        __syncwarp();
+        emit::sort_ids(lane, c.hist, S.rtmp, S.psrc2, nfull + 1, a.key_shift);
+        if (first) {
+            const int nR = 1 + nfull;
+            int64_t rec = 0;
+            const int64_t pos = emit::reserve(a, lane, 2 + (int64_t)nR + d, &rec);
+            if (pos >= 0) {
+                int32_t *o = a.out_ids + pos;
+                if (lane == 0) {
+                    a.out_offsets[rec] = pos;
+                    o[0] = nR;
+                    o[1] = d;
+                }
+                for (int k = lane; k < nR; k += 32) o[2 + k] = S.rtmp[k];
+                for (int k = lane; k < d; k += 32) o[2 + nR + k] = Ln[k];
+                __syncwarp();
             }
-            for (int k = lane; k < nfull; k += 32) o[3 + k] = S.rtmp[k];
-            for (int k = lane; k < d; k += 32) o[2 + nR + k] = Ln[k];
-        } else if (lane == 0) {
-            set_error(a, MBE_ERR_OUTPUT_FULL);
         }
     }
     if (pn == 0) {
@@ -1314,10 +1307,8 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     zero_words(c, D.Q, (int64_t)d * QW);
     if (qn > 0) rows_to_columns(c, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
     rows_to_columns(c, D.rows, W, nullptr, pn, d, D.Q, QW, qn);
-    if (a.emit) {
-        if (lane == 0) D.R[0] = r;
-        for (int k = lane; k < nfull; k += 32) D.R[1 + k] = S.rtmp[k];
-    }
+    if (a.emit)
+        for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {
         FrameHdr h;
         h.m = d;

@@ -32,6 +32,7 @@
 // its frame is pushed, which is the order in which Algorithm 1 pops it
 // because the counts are fixed while L' is fixed.
 #include "mbe_bits.h"
+#include "mbe_emit.cuh"
 #include "mbe_internal.h"
 
 namespace mbe {
@@ -468,32 +469,24 @@ __device__ __forceinline__ uint64_t sum_keys_v(Ctx &c, const int32_t *Lid, uint6
     return warp_sum64(s);
 }
 
-// Appends one biclique to the caller's output buffer: |R|, |L|, R ids, L ids.
-__device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase, int nRbase, int x_id,
-                              const int32_t *rfull, int nfull, const int32_t *Lid, uint64_t Lw, int W, int mL)
+// Appends one biclique to the caller's output buffer: |R|, |L|, R ids, L ids,
+// each side ascending. R' is the merge of the frame's R (ascending) with
+// B[0..nB) (x and the candidates that joined R', sorted); L' is the ids of
+// L selected by L' (lane w holds word w), in L's ascending id order.
+__device__ void emit_biclique(const SearchArgs &a, Ctx &c, const int32_t *Rbase, int nRbase, const int32_t *B,
+                              int nB, const int32_t *Lid, uint64_t Lw, int W, int mL)
 {
-    int nR = nRbase + 1 + nfull;
-    int64_t need = 2 + nR + mL;
-    unsigned long long pos = 0, b = 0;
-    if (c.lane == 0) {
-        pos = atomicAdd(a.used_ids, (unsigned long long)need);
-        b = atomicAdd(a.used_bic, 1ULL);
-    }
-    pos = __shfl_sync(kFull, pos, 0);
-    b = __shfl_sync(kFull, b, 0);
-    if ((int64_t)b >= a.cap_bic || (int64_t)(pos + need) > a.cap_ids) {
-        if (c.lane == 0) set_error(a, MBE_ERR_OUTPUT_FULL);
-        return;
-    }
+    const int nR = nRbase + nB;
+    int64_t rec = 0;
+    const int64_t pos = emit::reserve(a, c.lane, 2 + (int64_t)nR + mL, &rec);
+    if (pos < 0) return;
     int32_t *o = a.out_ids + pos;
     if (c.lane == 0) {
-        a.out_offsets[b] = (int64_t)pos;
+        a.out_offsets[rec] = pos;
         o[0] = nR;
         o[1] = mL;
-        o[2 + nRbase] = x_id;
     }
-    for (int k = c.lane; k < nRbase; k += 32) o[2 + k] = Rbase[k];
-    for (int k = c.lane; k < nfull; k += 32) o[3 + nRbase + k] = rfull[k];
+    emit::merge_into(c.lane, Rbase, nRbase, B, nB, o + 2);
     compact_ids(c, Lid, Lw, W, o + 2 + nR);
 }
 
@@ -592,7 +585,13 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 
     uint64_t t_build = tnow(a);
     if (a.emit || pn > 0) prepare_masks(c, Lw, W);
-    if (a.emit) emit_biclique(a, c, F.R, F.h->nR, xg, S.rtmp, nfull, F.Lid, Lw, W, mp);
+    if (a.emit) {
+        // B = {x} and the candidates that joined R', ascending
+        if (lane == 0) S.rtmp[nfull] = xg;
+        __syncwarp();
+        emit::sort_ids(lane, c.hist, S.rtmp, S.psrc2, nfull + 1, a.key_shift);
+        emit_biclique(a, c, F.R, F.h->nR, S.rtmp, nfull + 1, F.Lid, Lw, W, mp);
+    }
     if (pn == 0) {
         if (lane == 0) tadd(a, c, 2, t_build);
         return nullptr;
@@ -617,12 +616,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
     compact_ids(c, F.Lid, Lw, W, D.Lid);
     build_child_rows(c, F.rows, W, S.qsrc, qn, S.psrc, pn, D.rows, Wd);
-    if (a.emit) {
-        int nr0 = F.h->nR;
-        for (int k = lane; k < nr0; k += 32) D.R[k] = F.R[k];
-        if (lane == 0) D.R[nr0] = xg;
-        for (int k = lane; k < nfull; k += 32) D.R[nr0 + 1 + k] = S.rtmp[k];
-    }
+    if (a.emit) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
     if (lane == 0) {
         FrameHdr h;
         h.m = mp;
@@ -799,29 +793,26 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     }
 
     prepare_masks(c, Lw, W);
-    if (a.emit && first) {
-        // L' ids are N(r) itself
-        int nR = 1 + nfull;
-        int64_t need = 2 + nR + d;
-        unsigned long long pos = 0, b = 0;
-        if (lane == 0) {
-            pos = atomicAdd(a.used_ids, (unsigned long long)need);
-            b = atomicAdd(a.used_bic, 1ULL);
-        }
-        pos = __shfl_sync(kFull, pos, 0);
-        b = __shfl_sync(kFull, b, 0);
-        if ((int64_t)b < a.cap_bic && (int64_t)(pos + need) <= a.cap_ids) {
-            int32_t *o = a.out_ids + pos;
-            if (lane == 0) {
-                a.out_offsets[b] = (int64_t)pos;
-                o[0] = nR;
-                o[1] = d;
-                o[2] = r;
+    if (a.emit) {
+        // R' = {r} and the candidates that joined it, ascending; L' = N(r)
+        if (lane == 0) S.rtmp[nfull] = r;
+        __syncwarp();
+        emit::sort_ids(lane, c.hist, S.rtmp, S.psrc2, nfull + 1, a.key_shift);
+        if (first) {
+            const int nR = 1 + nfull;
+            int64_t rec = 0;
+            const int64_t pos = emit::reserve(a, lane, 2 + (int64_t)nR + d, &rec);
+            if (pos >= 0) {
+                int32_t *o = a.out_ids + pos;
+                if (lane == 0) {
+                    a.out_offsets[rec] = pos;
+                    o[0] = nR;
+                    o[1] = d;
+                }
+                for (int k = lane; k < nR; k += 32) o[2 + k] = S.rtmp[k];
+                for (int k = lane; k < d; k += 32) o[2 + nR + k] = G.u_adj[ro + k];
+                __syncwarp();
             }
-            for (int k = lane; k < nfull; k += 32) o[3 + k] = S.rtmp[k];
-            for (int k = lane; k < d; k += 32) o[2 + nR + k] = G.u_adj[ro + k];
-        } else if (lane == 0) {
-            set_error(a, MBE_ERR_OUTPUT_FULL);
         }
     }
     if (pn == 0) {
@@ -846,10 +837,8 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
     for (int k = lane; k < d; k += 32) D.Lid[k] = G.u_adj[ro + k];
     build_child_rows(c, S.urows, W, S.qsrc, qn, S.psrc, pn, D.rows, W);
-    if (a.emit) {
-        if (lane == 0) D.R[0] = r;
-        for (int k = lane; k < nfull; k += 32) D.R[1 + k] = S.rtmp[k];
-    }
+    if (a.emit)
+        for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {
         FrameHdr h;
         h.m = d;

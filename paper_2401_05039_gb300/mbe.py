@@ -165,6 +165,11 @@ class Graph:
         device = (not isinstance(u_off, np.ndarray)) and bool(getattr(u_off, "is_cuda", False))
         if isinstance(u_off, np.ndarray):
             u_off, u_adj, v_off, v_adj = (np.ascontiguousarray(a, dtype=np.int32) for a in (u_off, u_adj, v_off, v_adj))
+        if device:
+            _check_device_graph(int(nU), int(nV), u_off, u_adj, v_off, v_adj)
+        elif (int(u_off.shape[0]) != int(nU) + 1 or int(v_off.shape[0]) != int(nV) + 1
+              or int(u_adj.shape[0]) != int(v_adj.shape[0])):
+            raise MBEError(1, "u_off needs nU + 1 entries, v_off nV + 1, and u_adj / v_adj one per edge")
         self._keep = (u_off, u_adj, v_off, v_adj)
         h = _P()
         nE = int(u_adj.shape[0])
@@ -265,8 +270,24 @@ def copy_bandwidth(nbytes: int, iters: int = 5, stream=None) -> float:
     return out.value
 
 
+def _check_device_graph(nU, nV, u_off, u_adj, v_off, v_adj):
+    """Shape, dtype and placement of a graph given as device tensors (the library reads raw pointers)."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t in (("u_off", u_off), ("u_adj", u_adj), ("v_off", v_off), ("v_adj", v_adj)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+            raise MBEError(1, f"{name} must be a CUDA tensor on the current device (cuda:{dev})")
+        if t.dtype != torch.int32 or t.dim() != 1 or not t.is_contiguous():
+            raise MBEError(1, f"{name} must be a contiguous 1-D int32 tensor")
+    if nU < 0 or nV < 0 or u_off.numel() != nU + 1 or v_off.numel() != nV + 1:
+        raise MBEError(1, "u_off needs nU + 1 entries and v_off nV + 1")
+    if u_adj.numel() != v_adj.numel():
+        raise MBEError(1, "u_adj and v_adj must have the same length (one entry per edge)")
+
+
 def enumerate_noalloc(nU, nV, u_off, u_adj, v_off, v_adj, stream=None, check=True) -> Result:
     """mbe_enumerate_noalloc on DEVICE arrays (torch CUDA tensors); allocates nothing."""
+    _check_device_graph(int(nU), int(nV), u_off, u_adj, v_off, v_adj)
     r = Result()
     st = load().mbe_enumerate_noalloc(int(nU), int(nV), int(u_adj.shape[0]), _ptr(u_off), _ptr(u_adj), _ptr(v_off),
                                       _ptr(v_adj), _stream_handle(stream), ctypes.byref(r))

@@ -119,3 +119,56 @@ def test_batch_size_classes():
     assert m.batch_class(200, 16, 10) == 4
     assert m.batch_class(16, 600, 10) == 2
     assert m.batch_class(512, 2048, 200000) == 7
+
+
+def _bad_host_graphs():
+    """Host graphs whose offsets or ids fall outside the arrays (never sent to a device)."""
+    import numpy as np
+    from tests import helpers as H
+    g = H.random_graph(np.random.default_rng(1), 10, 12, 0.4)
+    arrs = [np.ascontiguousarray(a, dtype=np.int32).copy() for a in (g.u_off, g.u_adj, g.v_off, g.v_adj)]
+    cases = []
+
+    def case(name, k, idx, val):
+        a = [x.copy() for x in arrs]
+        a[k][idx] = val
+        cases.append((name, a))
+
+    case("u id = nV", 1, 0, g.nV)
+    case("u id negative", 1, 3, -5)
+    case("v id = nU", 3, 2, g.nU)
+    case("u offset past nE", 0, 4, g.nE + 7)
+    case("u offsets decrease", 0, 5, int(arrs[0][4]) - 1 if arrs[0][4] > 0 else -1)
+    case("v offset negative", 2, 3, -1)
+    case("u_off[0] != 0", 0, 0, 1)
+    case("v_off[nV] != nE", 2, g.nV, g.nE - 1)
+    return g, cases
+
+
+def test_host_graph_out_of_range_rejected_before_any_device_work():
+    # host input is range-checked on the host: MBE_ERR_INVALID_GRAPH comes
+    # back before any CUDA call, so this runs without a GPU
+    import paper_2401_05039_gb300 as m
+    lib = m.load()
+    g, cases = _bad_host_graphs()
+    for name, (uo, ua, vo, va) in cases:
+        h = ctypes.c_void_p()
+        st = lib.mbe_graph_create(g.nU, g.nV, g.nE, uo.ctypes.data, ua.ctypes.data, vo.ctypes.data, va.ctypes.data,
+                                  0, None, ctypes.byref(h))
+        assert st == 2 and not h.value, name
+
+
+def test_host_batch_out_of_range_rejected_before_any_device_work():
+    # the same corruptions in the second graph of a packed batch (host arrays)
+    import synth
+    import paper_2401_05039_gb300 as m
+    g, cases = _bad_host_graphs()
+    for name, (uo, ua, vo, va) in cases:
+        b = synth.pack([g, g])
+        e0, us, vs = int(b.edge_off[1]), int(b.u_off_start[1]), int(b.v_off_start[1])
+        b.u_off[us:us + g.nU + 1] = uo
+        b.v_off[vs:vs + g.nV + 1] = vo
+        b.u_adj[e0:e0 + g.nE] = ua
+        b.v_adj[e0:e0 + g.nE] = va
+        per, tot = m.enumerate_batch(b, check=False)
+        assert tot.status == 2, name

@@ -59,9 +59,55 @@ def test_er200x300_full_set(mbe, golden_dir, layout):
     r = G.enumerate(emit=1, bicliques=buf.buf, layout=layout)
     torch.cuda.synchronize()
     assert gpu_tuple(r) == (c, h, n, b)
-    got = buf.decode()
+    got = raw_records(buf)
     assert len(got) == c
-    assert H.canon(got) == H.canon(rec)
+    assert all(ascending(R) and ascending(L) for R, L in got)
+    assert sorted(got) == sorted(rec)
+    G.close()
+
+
+def raw_records(buf):
+    """The records as the library wrote them (no sorting here): [(R, L), ...]."""
+    n = int(buf.buf.n_bicliques_written)
+    ids = buf.ids.cpu().numpy()
+    out = []
+    for o in buf.offsets[:n].cpu().numpy().tolist():
+        nr, nl = int(ids[o]), int(ids[o + 1])
+        out.append((tuple(ids[o + 2:o + 2 + nr].tolist()), tuple(ids[o + 2 + nr:o + 2 + nr + nl].tolist())))
+    return out
+
+
+def ascending(t):
+    return all(x < y for x, y in zip(t, t[1:]))
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_output_full_keeps_exact_totals_and_reports_sizes(mbe, layout):
+    # a buffer that is too small: the call returns MBE_ERR_OUTPUT_FULL with
+    # count, hash, nodes and bytes still equal to the oracle's, and the sizes
+    # the whole output needs; a second call with those sizes returns every
+    # biclique, each written as R ascending then L ascending
+    import torch
+    g = synth.workload("er200x300")
+    c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
+    need_ids = sum(2 + len(R) + len(L) for R, L in rec)
+    G = mbe.Graph.from_synth(g)
+    for cap_ids, cap_bic in [(200000, 100), (1000, 10000), (0, 0)]:
+        small = mbe.Bicliques.allocate(cap_ids, cap_bic)
+        r = G.enumerate(emit=1, bicliques=small.buf, layout=layout, check=False)
+        torch.cuda.synchronize()
+        assert r.status == 5, (cap_ids, cap_bic)
+        assert gpu_tuple(r) == (c, h, n, b)
+        assert small.buf.n_bicliques_written == c
+        assert small.buf.n_ids_written == need_ids
+    full = mbe.Bicliques.allocate(need_ids, c)
+    r = G.enumerate(emit=1, bicliques=full.buf, layout=layout)
+    torch.cuda.synchronize()
+    assert r.status == 0 and gpu_tuple(r) == (c, h, n, b)
+    assert full.buf.n_ids_written == need_ids and full.buf.n_bicliques_written == c
+    got = raw_records(full)
+    assert all(ascending(R) and ascending(L) for R, L in got)
+    assert sorted(got) == sorted(rec)
     G.close()
 
 
@@ -125,6 +171,28 @@ def test_emit_matches_closure(mbe, layout):
     assert all(H.is_closed_pair(g, R, L, adj) for R, L in got)
     assert oracle.biclique_hash(got) == r.hash
     G.close()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_emit_records_sorted_on_wide_sides(mbe, layout):
+    # sides longer than a warp (the radix-sort path of the R merge) and long
+    # L sides: the records equal the oracle's, each side already ascending
+    import torch
+    graphs = [H.complete(70, 5), H.complete(3, 200), H.crown(9),
+              synth.planted(600, 700, 0.02, 6, (30, 60), (8, 14), 0.3, 5),
+              H.random_graph(np.random.default_rng(12), 16, 700, 0.45)]
+    for g in graphs:
+        c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
+        need = sum(2 + len(R) + len(L) for R, L in rec)
+        G = mbe.Graph.from_synth(g)
+        buf = mbe.Bicliques.allocate(need, c)
+        r = G.enumerate(emit=1, bicliques=buf.buf, layout=layout)
+        torch.cuda.synchronize()
+        got = raw_records(buf)
+        assert gpu_tuple(r) == (c, h, n, b), g.name
+        assert all(ascending(R) and ascending(L) for R, L in got), g.name
+        assert sorted(got) == sorted(rec), g.name
+        G.close()
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
