@@ -40,6 +40,8 @@ BYTES_MODEL = 2
 def _row(r, with_bytes=True):
     out = {"count": int(r[0]), "hash": hex(int(r[1])), "nodes": int(r[2])}
     out["bytes"] = int(r[3]) if with_bytes else None
+    if len(r) > 4:
+        out["bytes_b"] = int(r[4])  # the second byte model (bitset rows or reverse-scanned lists)
     return out
 
 
@@ -68,7 +70,7 @@ def set_digest(records):
 
 def whole_graph(name, g, threads, n_heavy=16, n_random=48, records=False):
     t0 = time.time()
-    pr = oracle.per_root(g, nthreads=threads)
+    pr = oracle.per_root(g, nthreads=threads, bytes_b=True)
     out = {"workload": name, "graph": _graph_info(g),
            "total": _row(pr.sum(axis=0, dtype=np.uint64)), "oracle_seconds": round(time.time() - t0, 1),
            "oracle_threads": threads}
@@ -92,7 +94,7 @@ def sampled_roots(name, g, threads, n_random=40, n_top_degree=8):
     upper = live[deg[live] >= np.quantile(deg[live], 0.9)]
     top = rng.choice(upper, size=min(n_top_degree, upper.size), replace=False)
     roots = np.array(sorted(set(rand.tolist()) | set(top.tolist())), dtype=np.int32)
-    pr = oracle.per_root(g, roots=roots, nthreads=threads)
+    pr = oracle.per_root(g, roots=roots, nthreads=threads, bytes_b=True)
     return {"workload": name, "graph": _graph_info(g), "total": None,
             "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": threads,
             "per_root": {str(int(r)): _row(pr[i]) for i, r in enumerate(roots)}}
@@ -162,17 +164,18 @@ def prefix_sample(name, g, threads, seed=20240110, batch=256, keep_rows=300, pro
     rng = np.random.default_rng(seed)
     live = np.nonzero(np.diff(g.u_off) > 0)[0]
     perm = rng.permutation(live).astype(np.int32)
-    rows = np.zeros((0, 4), dtype=np.uint64)
+    rows = np.zeros((0, 5), dtype=np.uint64)
     model = BYTES_MODEL
     if progress and os.path.exists(progress):
         d = np.load(progress)
-        if int(d["seed"]) == seed and d["digest"].item() == g.digest():
+        # rows without the second byte model's column are not resumed
+        if int(d["seed"]) == seed and d["digest"].item() == g.digest() and d["rows"].shape[1] == 5:
             rows = d["rows"]
             model = int(d["bytes_model"]) if "bytes_model" in d else 1
     t0 = time.time()
     while rows.shape[0] < perm.size and (time_budget is None or time.time() - t0 < time_budget):
         k = rows.shape[0]
-        part = oracle.per_root(g, roots=perm[k:k + batch], nthreads=threads)
+        part = oracle.per_root(g, roots=perm[k:k + batch], nthreads=threads, bytes_b=True)
         rows = np.concatenate([rows, part])
         if progress:
             np.savez(progress + ".tmp.npz", rows=rows, seed=seed, digest=np.array(g.digest()),
@@ -182,11 +185,11 @@ def prefix_sample(name, g, threads, seed=20240110, batch=256, keep_rows=300, pro
     K = rows.shape[0]
     pick = np.random.default_rng(seed + 1).choice(K, size=min(keep_rows, K), replace=False) if K else []
     pick = sorted(int(x) for x in pick)
-    total = rows.sum(axis=0, dtype=np.uint64) if K else np.zeros(4, np.uint64)
+    total = rows.sum(axis=0, dtype=np.uint64) if K else np.zeros(5, np.uint64)
     fresh = model == BYTES_MODEL
     if not fresh and pick:
         # rows from an older byte model: the kept rows are run again, whole
-        again = oracle.per_root(g, roots=perm[pick], nthreads=threads)
+        again = oracle.per_root(g, roots=perm[pick], nthreads=threads, bytes_b=True)
         assert (again[:, :3] == rows[pick, :3]).all(), "count/hash/nodes changed between oracle versions"
         rows = rows.copy()
         rows[pick] = again

@@ -51,11 +51,15 @@ def _traces(golden_dir):
 def test_hand_traces(golden_dir):
     for t in _traces(golden_dir):
         g = H.graph(t["nU"], t["nV"], t["edges"])
-        c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
+        c, h, n, b, bb, rec = oracle.enumerate_graph(g, records=True, bytes_b=True)
         expect = [(tuple(r), tuple(l)) for r, l in t["bicliques"]]
         assert c == t["count"], t["name"]
         assert n == t["nodes"], t["name"]
         assert b == t["bytes"], t["name"]
+        assert bb == t["bytes_b"], t["name"]
+        # the per-root driver adds up to the same two byte counts
+        pr = oracle.per_root(g, bytes_b=True)
+        assert int(pr[:, 3].sum()) == b and int(pr[:, 4].sum()) == bb, t["name"]
         assert H.canon(rec) == H.canon(expect), t["name"]
         assert h == sm_hash(expect)
 
@@ -73,6 +77,8 @@ def test_complete_bipartite_one_biclique(a, b):
     assert n == a
     # each top-level node reads N(x) and the b lists N(w) of length a
     assert byt == a * 4 * (b + b * a)
+    # no node below the top level: the second byte model counts the same
+    assert oracle.enumerate_graph(g, bytes_b=True)[4] == byt
 
 
 @pytest.mark.parametrize("n", [1, 2, 5, 40])
