@@ -96,7 +96,9 @@ int mbe_graph_info(const mbe_graph *g, int32_t *nU, int32_t *nV, int64_t *nE, in
  * builds, sum of |L'|, sum of parent row words, sum of parent candidates;
  * [22] ns in the check against Q, [23] ns building child columns, of which
  * [24] forming Q', [25] copying or compressing the parent's columns, [26]
- * transposing P'; [27] child builds that copied the columns uncompressed.
+ * transposing P'; [27] child builds that copied the columns uncompressed;
+ * both layouts: [28] ns from the launch to the end of the worker's last
+ * task, [29] ns the worker spent idle between tasks (before that end).
  * The timers read the global timer and slow the search. This copies up to
  * max_workers of them (MBE_TRACE_WORDS uint64 each) to `host` and
  * returns how many were copied. MBE_DEADLINE_MS bounds any single launch
@@ -171,7 +173,10 @@ int mbe_model_train(mbe_model *m, const float *d_feat, const float *d_target, in
 typedef struct {
     int32_t block_threads;    /* threads per block, multiple of 32, 32..1024; 0 = auto */
     int32_t blocks_per_sm;    /* resident blocks per SM for the persistent launch; 0 = auto */
-    int32_t bitset_max_words; /* widest root-local bitset row, in 64-bit words (1..32); 0 = 32 */
+    int32_t bitset_max_words; /* bitset limit, in 64-bit words (1..32; 0 = 32): a level set of at most
+                                 64 * bitset_max_words vertices is packed into bitset rows; a wider one
+                                 (a root of higher degree, or a node below it) is kept as sorted id
+                                 lists, and its counts come from a reverse scan over L' (Sec. III-D) */
     int32_t steal;            /* 1 = busy workers split their shallowest frame for idle ones (Sec. III-C) */
     int32_t schedule;         /* 0 = static execution order (descending degree); 1 = learned: roots by
                                  descending predicted cost, predicted-heavy roots split into up to 32
@@ -245,9 +250,10 @@ typedef struct {
  * one persistent launch of warp workers). opts may be NULL (defaults).
  * out receives count, hash, nodes and timings; bicliques may be NULL
  * (count + hash only). The result is independent of every option except
- * root_begin/root_end (which select a shard of roots; shards add up).
- * Limit: a root with more than 64 * bitset_max_words (at most 2,048)
- * neighbours returns MBE_ERR_UNSUPPORTED (the launch stops cleanly).
+ * root_begin/root_end (which select a shard of roots; shards add up). Any
+ * degree is accepted: level sets wider than the bitset limit run on sorted
+ * lists (a second variant of the search kernel, launched only for graphs
+ * with such roots).
  */
 int mbe_enumerate(const mbe_graph *g, const mbe_options *opts, void *stream, mbe_result *out,
                   mbe_biclique_buffer *bicliques);
@@ -267,6 +273,7 @@ typedef struct {
     int32_t layout;        /* frame layout as mbe_options.layout (0 = auto) */
     int32_t reserved;
     double tuned_ms;       /* time the autotuner measured for this choice on its sample */
+    double default_ms;     /* time of the default launch parameters on the same sample */
 } mbe_class_params;
 
 /* Size class of one graph (see MBE_N_CLASSES). */
@@ -274,10 +281,14 @@ int mbe_batch_class(int32_t nU, int32_t nV, int64_t nE);
 
 /*
  * Autotuner (no counterpart in the paper): for every size class present in
- * the batch, times a set of launch shapes (block size, blocks per SM,
- * stealing on/off, frame layout rows/columns) on an evenly spaced sample of the class (at least
- * sample_per_class graphs and enough graphs for 16 roots per worker, or the
- * whole class) and writes the fastest into table[class] (valid = 1).
+ * the batch, times a set of launch shapes -- 8, 12 or 16 resident warps per
+ * SM in blocks of 64 to 512 threads, work stealing on or off, the row or
+ * the column frame layout -- on a sample of the class's (graph, root) tasks
+ * (every k-th task of its heavy-first order, about sample_per_class tasks
+ * per default worker, or the whole class; halved while one run takes more
+ * than 250 ms, down to one task per worker), every shape once and the two
+ * fastest again, and writes the fastest into table[class] (valid = 1,
+ * tuned_ms = its time on the sample, default_ms = the defaults' time there).
  * Arguments as in mbe_enumerate_batch; table has MBE_N_CLASSES entries.
  */
 int mbe_autotune_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t *nU, const int32_t *nV,
@@ -296,7 +307,9 @@ int mbe_autotune_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t 
  * into size classes; each class is one persistent launch over its (graph,
  * root) tasks with the parameters of opts->class_params (autotuned) or the
  * defaults; the launches of all classes are captured in one CUDA graph and
- * replayed. Limits: per graph nU <= 65536 and every degree <= 2048.
+ * replayed. per_graph[i].device_ms is the device time of the launch that
+ * ran graph i (its size class); total->device_ms that of the whole batch.
+ * Limits: per graph nU <= 65536 and every degree <= 2048.
  */
 int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t *nU, const int32_t *nV,
                         const int64_t *u_off_start, const int64_t *v_off_start, const int32_t *u_off_cat,

@@ -153,6 +153,37 @@ def batch(name, threads, n_graphs=4096, budget_count=2.0e5, n_heavy_graphs=12, r
             "oracle_seconds": round(time.time() - t0, 1), "oracle_threads": threads}
 
 
+def batch_rest_roots(path, threads, back=(2, 16, 48)):
+    """Per-root rows for the batch graphs the oracle cannot finish whole.
+
+    For every graph of the batch without a stored whole-graph row, the
+    top-level candidates at pop positions n - b for b in `back` (n = number
+    of non-isolated roots): the last pops have the smallest subtrees, so
+    these rows stay within seconds of oracle time each while still covering
+    nodes below the top level. Added to the existing batch golden in place.
+    """
+    with open(path) as f:
+        gold = json.load(f)
+    t0 = time.time()
+    done = set(int(k) for k in gold["per_graph"])
+    rest = [i for i in range(gold["n_graphs"]) if i not in done]
+    out = {}
+    for i in rest:
+        g = synth.batch_graph(3 + i)
+        seq = oracle.root_order(g)
+        n = len(seq)
+        roots = np.array(sorted({int(seq[n - b]) for b in back if n - b >= 0}), dtype=np.int32)
+        pr = oracle.per_root(g, roots=roots, nthreads=threads)
+        out[str(i)] = {str(int(r)): _row(pr[k]) for k, r in enumerate(roots)}
+    gold["rest_graph_roots"] = out
+    gold["rest_graph_roots_about"] = ("graphs without a whole-graph oracle row: per-root rows of the top-level pops at "
+                                      f"positions n - {', n - '.join(str(b) for b in back)} of the (degree, id) order")
+    gold["rest_oracle_seconds"] = round(time.time() - t0, 1)
+    with open(path, "w") as f:
+        json.dump(gold, f, indent=1, sort_keys=True)
+    return len(out)
+
+
 def prefix_sample(name, g, threads, seed=20240110, batch=256, keep_rows=300, progress=None, time_budget=None):
     """Per-root oracle rows for the roots in a seeded random order, in batches, resumable.
 
@@ -208,8 +239,14 @@ def main():
     ap.add_argument("--prefix", action="store_true", help="resumable seeded-order per-root run (large graphs)")
     ap.add_argument("--progress", default=None, help="progress file for --prefix")
     ap.add_argument("--budget", type=float, default=None, help="seconds to spend in this --prefix invocation")
+    ap.add_argument("--batch-rest", action="store_true",
+                    help="add per-root rows of the batch graphs without whole-graph rows to batch4096.json")
     args = ap.parse_args()
     os.makedirs(GOLDEN, exist_ok=True)
+    if args.batch_rest:
+        n = batch_rest_roots(os.path.join(GOLDEN, "batch4096.json"), args.threads)
+        print(f"batch4096: per-root rows for {n} graphs", flush=True)
+        return
     for name in args.names:
         t0 = time.time()
         if args.prefix:

@@ -203,7 +203,8 @@ cudaStream_t capture_stream()
 // each; with `capture` the whole sequence is captured into a CUDA graph and
 // launched as one. *ms = device time of the sequence.
 int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector<ClassLaunch> &cl,
-                const mbe_options &o, cudaStream_t s, bool capture, double *ms, uint64_t *donations)
+                const mbe_options &o, cudaStream_t s, bool capture, double *ms, uint64_t *donations,
+                std::vector<double> *class_ms = nullptr)
 {
     Workspace &ws = device_workspace();
     int64_t nc = 0, urow = 0, frame = 0, n_tasks = 0;
@@ -232,7 +233,7 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
 
     int stack_factor = 2;
     for (int attempt = 0; attempt < 4; ++attempt) {
-        int st = ensure_workspace(ws, nc, urow, frame, max_nU, big, o.arena_bytes, stack_factor);
+        int st = ensure_workspace(ws, nc, urow, frame, max_nU, big, o.arena_bytes, stack_factor, kMaxBitsetWords * 64);
         if (st != MBE_OK) return st;
         if (ws.marks_dirty) {
             e = cudaMemsetAsync(ws.mark, 0xff, sizeof(int32_t) * (size_t)ws.mark_stride * ws.n_warps, s);
@@ -269,6 +270,7 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
             a.mark_stride = ws.mark_stride;
             a.n_cand_cap = ws.n_cand_cap;
             a.urow_bytes = ws.urow_bytes;
+            a.lbuf_cap = ws.lbuf_cap;
             Ctl *c = d.ctls + k;
             a.cursor = &c->cursor;
             a.n_idle = &c->n_idle;
@@ -283,7 +285,7 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
             const int wpb = cl[k].shape.threads / 32;
             blocks[k] = std::min(cl[k].shape.blocks, ws.n_warps / wpb);
             a.n_warps = blocks[k] * wpb;
-            a.max_words = 32;
+            a.max_words = kMaxBitsetWords;
             a.per_task_owner = d.owner;
             a.per_root_mode = 2;
             a.emit = 0;
@@ -293,12 +295,19 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
+        // one event after every class launch (inside a capture: external
+        // event nodes, recorded when the graph runs) for per-class times
+        std::vector<cudaEvent_t> ce(plans.size(), nullptr);
+        for (auto &x : ce) cudaEventCreate(&x);
         auto enqueue = [&](cudaStream_t q) -> cudaError_t {
             cudaError_t r = cudaMemsetAsync(d.ctls, 0, sizeof(Ctl) * MBE_N_CLASSES, q);
             for (size_t k = 0; k < plans.size() && r == cudaSuccess; ++k) {
-                if (args[k].n_tasks == 0) continue;
-                r = cudaMemsetAsync(ws.slot_state, 0, sizeof(int32_t) * (size_t)ws.n_warps, q);
-                if (r == cudaSuccess) r = launch_layout(args[k], blocks[k], cl[k].shape, q);
+                if (args[k].n_tasks > 0) {
+                    r = cudaMemsetAsync(ws.slot_state, 0, sizeof(int32_t) * (size_t)ws.n_warps, q);
+                    if (r == cudaSuccess) r = launch_layout(args[k], blocks[k], cl[k].shape, q);
+                }
+                if (r == cudaSuccess)
+                    r = capture ? cudaEventRecordWithFlags(ce[k], q, cudaEventRecordExternal) : cudaEventRecord(ce[k], q);
             }
             return r;
         };
@@ -324,6 +333,15 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         float t = 0.f;
         if (e == cudaSuccess) cudaEventElapsedTime(&t, e0, e1);
+        if (class_ms) {
+            class_ms->assign(plans.size(), -1.0);
+            for (size_t k = 0; k < plans.size() && e == cudaSuccess; ++k) {
+                float tk = 0.f;
+                if (cudaEventElapsedTime(&tk, k == 0 ? e0 : ce[k - 1], ce[k]) == cudaSuccess) (*class_ms)[k] = tk;
+                else cudaGetLastError();
+            }
+        }
+        for (auto &x : ce) cudaEventDestroy(x);
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         cudaEventDestroy(e0);
@@ -346,6 +364,9 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
     }
     return MBE_ERR_ARENA_FULL;
 }
+
+// Longest single timing the autotuner spends on one class sample.
+constexpr double kTuneTargetMs = 250.0;
 
 int check_args(const HostBatch &b)
 {
@@ -416,7 +437,10 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
     }
     double ms = 0.0;
     uint64_t don = 0;
-    st = plans.empty() ? MBE_OK : run_classes(d, plans, cl, o, s, true, &ms, &don);
+    std::vector<double> cms;
+    st = plans.empty() ? MBE_OK : run_classes(d, plans, cl, o, s, true, &ms, &don, &cms);
+    std::vector<double> ms_of_class(MBE_N_CLASSES, 0.0);
+    for (size_t k = 0; k < plans.size() && k < cms.size(); ++k) ms_of_class[plans[k].cls] = cms[k];
     std::vector<unsigned long long> res((size_t)n_graphs * 4, 0);
     if (st == MBE_OK || st == MBE_ERR_TIMEOUT) {
         cudaError_t e = cudaMemcpy(res.data(), d.owner, sizeof(unsigned long long) * 4 * (size_t)n_graphs,
@@ -431,6 +455,7 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
         r.hash = res[4 * (size_t)i + 1];
         r.nodes = res[4 * (size_t)i + 2];
         r.bytes_alg = res[4 * (size_t)i + 3];
+        r.device_ms = ms_of_class[class_of(nU[i], nV[i], edge_off[i + 1] - edge_off[i])];
         r.status = st;
         c += r.count;
         h += r.hash;
@@ -469,52 +494,81 @@ int mbe_autotune_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t 
     }
     mbe_options o;
     mbe_default_options(&o);
-    // candidates: (threads, blocks per SM, steal, frame layout)
-    const int cand[][4] = {{64, 8, 1, kLayoutRows},     {128, 4, 1, kLayoutRows},    {256, 2, 1, kLayoutRows},
-                           {512, 1, 1, kLayoutRows},    {256, 2, 0, kLayoutRows},    {64, 8, 1, kLayoutColumns},
-                           {128, 4, 1, kLayoutColumns}, {256, 2, 1, kLayoutColumns}, {512, 1, 1, kLayoutColumns},
-                           {256, 2, 0, kLayoutColumns}};
+    // candidates: (threads, blocks per SM, steal, frame layout) -- 8, 12 and
+    // 16 resident warps per SM (the register budget of the search kernels
+    // allows 16 at most), work stealing on and off, both frame layouts
+    const int cand[][4] = {{256, 1, 1, kLayoutRows},    {128, 3, 1, kLayoutRows},    {256, 2, 1, kLayoutRows},
+                           {256, 2, 0, kLayoutRows},    {128, 3, 0, kLayoutRows},    {256, 1, 1, kLayoutColumns},
+                           {128, 3, 1, kLayoutColumns}, {256, 2, 1, kLayoutColumns}, {256, 2, 0, kLayoutColumns},
+                           {64, 8, 1, kLayoutRows},     {512, 1, 1, kLayoutRows}};
     const int n_cand = (int)(sizeof(cand) / sizeof(cand[0]));
     std::vector<std::vector<int32_t>> members(MBE_N_CLASSES);
     for (int32_t i = 0; i < n_graphs; ++i)
         members[class_of(nU[i], nV[i], edge_off[i + 1] - edge_off[i])].push_back(i);
     for (int k = 0; k < MBE_N_CLASSES && st == MBE_OK; ++k) {
         if (members[k].empty()) continue;
-        // an evenly spaced sample of the class in its heavy-first order
         ClassPlan full;
+        full.cls = k;
         plan_class(b, d, members[k], full);
-        std::vector<int32_t> order;
-        for (size_t t = 0; t < full.tgraph.size(); ++t)
-            if (order.empty() || order.back() != full.tgraph[t]) order.push_back(full.tgraph[t]);
-        // the sample must fill the GPU, or it measures launch overhead
-        // instead of throughput: at least sample_per_class graphs and at
-        // least 16 roots per default worker, spread evenly over the class
-        const int64_t want_roots = 16LL * shape_for(0, 0, kLayoutColumns).warps;
-        int64_t class_roots = (int64_t)full.troot.size();
-        size_t m = std::min<size_t>((size_t)sample_per_class, order.size());
-        if (class_roots > 0) {
-            size_t need = (size_t)((double)order.size() * std::min(1.0, (double)want_roots / (double)class_roots));
-            m = std::min(order.size(), std::max(m, need));
-        }
-        std::vector<int32_t> sample;
-        for (size_t j = 0; j < m; ++j) sample.push_back(order[j * order.size() / m]);
+        if (full.troot.empty()) continue;
+        // the sample: every step-th (graph, root) task of the class in its
+        // heavy-first order, about sample_per_class tasks per default worker
+        // (or the whole class), thinned by halves while one run of the default
+        // shape takes more than kTuneTargetMs, so that a class of heavy roots
+        // is tuned in seconds and not in minutes
+        const LaunchShape def = shape_for(0, 0, kLayoutColumns);
+        const int64_t want = (int64_t)sample_per_class * def.warps;
+        const int64_t nt = (int64_t)full.troot.size();
+        int64_t step = std::max<int64_t>(1, nt / std::max<int64_t>(want, 1));
         std::vector<ClassPlan> plans(1);
-        plans[0].cls = k;
-        plan_class(b, d, sample, plans[0]);
-        if (plans[0].troot.empty()) continue;
-        double best = 1e300;
+        ClassPlan &p = plans[0];
+        auto take = [&](int64_t stp) {
+            p = full;
+            p.troot.clear();
+            p.tgraph.clear();
+            for (int64_t t = 0; t < nt; t += stp) {
+                p.troot.push_back(full.troot[t]);
+                p.tgraph.push_back(full.tgraph[t]);
+            }
+        };
+        take(step);
+        auto time_of = [&](const mbe_class_params &prm, double *out) {
+            std::vector<ClassLaunch> cl(1, launch_for(&prm, o, p));
+            return run_classes(d, plans, cl, o, s, false, out, nullptr);
+        };
+        const mbe_class_params dflt{0, 0, 1, 1, 0, 0, 0.0};
+        double t_def = 0.0;
+        st = time_of(dflt, &t_def); // also sizes the workspace
+        if (st == MBE_OK) st = time_of(dflt, &t_def);
+        while (st == MBE_OK && t_def > kTuneTargetMs && (int64_t)p.troot.size() >= 2LL * def.warps) {
+            step *= 2;
+            take(step);
+            st = time_of(dflt, &t_def);
+        }
+        // every candidate once on the sample, then the two fastest again
+        std::vector<std::pair<double, int>> res;
         for (int c = 0; c < n_cand && st == MBE_OK; ++c) {
             mbe_class_params prm{cand[c][0], cand[c][1], cand[c][2], 1, cand[c][3], 0, 0.0};
-            std::vector<ClassLaunch> cl(1, launch_for(&prm, o, plans[0]));
-            double ms = 0.0, ms2 = 0.0;
-            st = run_classes(d, plans, cl, o, s, false, &ms, nullptr); // warm-up
-            if (st == MBE_OK) st = run_classes(d, plans, cl, o, s, false, &ms2, nullptr);
-            if (st == MBE_OK && ms2 < best) {
-                best = ms2;
+            if (launch_for(&prm, o, p).shape.threads != prm.block_threads) continue; // not on this device
+            double ms = 0.0;
+            st = time_of(prm, &ms);
+            if (st == MBE_OK) res.push_back({ms, c});
+        }
+        std::sort(res.begin(), res.end());
+        double best = 1e300;
+        for (size_t r = 0; r < res.size() && r < 2 && st == MBE_OK; ++r) {
+            const int c = res[r].second;
+            mbe_class_params prm{cand[c][0], cand[c][1], cand[c][2], 1, cand[c][3], 0, 0.0};
+            double ms = 0.0;
+            st = time_of(prm, &ms);
+            ms = std::min(ms, res[r].first);
+            if (st == MBE_OK && ms < best) {
+                best = ms;
                 table[k] = prm;
-                table[k].tuned_ms = ms2;
+                table[k].tuned_ms = ms;
             }
         }
+        table[k].default_ms = t_def;
     }
     d.release();
     return st;

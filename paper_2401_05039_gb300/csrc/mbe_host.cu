@@ -166,13 +166,14 @@ cudaError_t launch_layout(const SearchArgs &a, int blocks, const LaunchShape &sh
 
 // Sizes (and allocates when needed) the per-warp workspace for a launch.
 int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t frame_max, int32_t max_nU,
-                     const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor)
+                     const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor, int32_t max_deg)
 {
     // one entry more than the largest candidate set: a new R' list holds the
     // candidates that join R' and the popped vertex itself
     const int64_t ncap = std::max<int64_t>(nc_max + 1, 32);
     const int64_t urow = round_up(std::max<int64_t>(urow_max, 256), 256);
-    const int64_t scratch = scratch_layout_bytes(ncap, urow);
+    const int32_t dmax = std::max<int32_t>(max_deg, 32);
+    const int64_t scratch = scratch_layout_bytes(ncap, urow, dmax);
     int64_t stack = stack_bytes_req > 0 ? stack_bytes_req : (int64_t)stack_factor * frame_max + (256 << 10);
     stack = round_up(stack, 256);
     const int64_t arena = stack + scratch;
@@ -191,6 +192,7 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
         ws.scratch_bytes = scratch;
         ws.n_cand_cap = ncap;
         ws.urow_bytes = urow;
+        ws.lbuf_cap = dmax;
         return MBE_OK;
     }
     if (ws.arena) {
@@ -229,6 +231,7 @@ int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t fr
     ws.blocks = n_warps / (shape.threads / 32);
     ws.n_cand_cap = ncap;
     ws.urow_bytes = urow;
+    ws.lbuf_cap = dmax;
     ws.budget_limited = limited;
     return MBE_OK;
 }
@@ -242,7 +245,7 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
     int stack_factor = 2;
     for (int attempt = 0; attempt < 4; ++attempt) {
         int st = ensure_workspace(ws, in.nc_max, in.urow_max, in.frame_max, in.max_nU, shape, o.arena_bytes,
-                                  stack_factor);
+                                  stack_factor, in.max_deg);
         if (st != MBE_OK) return st;
         if (ws.marks_dirty) {
             MBE_TRY(cudaMemsetAsync(ws.mark, 0xff, sizeof(int32_t) * (size_t)ws.mark_stride * ws.n_warps, s));
@@ -277,6 +280,7 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         a.mark_stride = ws.mark_stride;
         a.n_cand_cap = ws.n_cand_cap;
         a.urow_bytes = ws.urow_bytes;
+        a.lbuf_cap = ws.lbuf_cap;
         a.cursor = &ws.ctl->cursor;
         a.n_idle = &ws.ctl->n_idle;
         a.outstanding = &ws.ctl->outstanding;
@@ -289,7 +293,8 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         const int wpb = shape.threads / 32;
         const int blocks = std::min(shape.blocks, ws.n_warps / wpb);
         a.n_warps = blocks * wpb;
-        a.max_words = o.bitset_max_words > 0 ? std::min(o.bitset_max_words, 32) : 32;
+        a.max_words = o.bitset_max_words > 0 ? std::min(o.bitset_max_words, kMaxBitsetWords) : kMaxBitsetWords;
+        a.lists = in.max_deg > 64 * a.max_words ? 1 : 0; // some root needs the sorted-list path
         a.totals = ws.ctl->totals;
         a.per_task_owner = in.per_owner;
         a.per_root_mode = in.per_mode;
@@ -370,7 +375,7 @@ int root_features(mbe_graph *g, float *d_feat, int32_t *d_raw, cudaStream_t s)
     mbe_options o;
     mbe_default_options(&o);
     int st = ensure_workspace(ws, g->nc_max, g->urow_max, g->frame_max, g->nU,
-                              choose_shape(o, resolve_layout(o.layout, g->max_deg_v)), 0, 2);
+                              choose_shape(o, resolve_layout(o.layout, g->max_deg_v)), 0, 2, g->max_deg_u);
     if (st != MBE_OK) return st;
     const int n = g->nU + g->nV;
     int32_t *tmp = nullptr, *raw = nullptr;
@@ -709,7 +714,7 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
                    bicliques->capacity_bicliques < 0))
         return set_status(out, MBE_ERR_INVALID_ARG);
     if (o.block_threads < 0 || o.blocks_per_sm < 0 || o.watchdog_ms < 0 || o.arena_bytes < 0 || o.layout < 0 ||
-        o.layout > kLayoutColumns)
+        o.layout > kLayoutColumns || o.bitset_max_words < 0)
         return set_status(out, MBE_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     if (g->nU == 0 || g->n_live == 0) return set_status(out, MBE_OK);
@@ -761,6 +766,7 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     in.n_owner = g->nU;
     in.per_mode = 1;
     in.layout = resolve_layout(o.layout, g->max_deg_v);
+    in.max_deg = g->max_deg_u;
     int st = run_search(device_workspace(), in, o, s, out, bicliques);
     if (out) out->prep_ms = prep_ms;
     return set_status(out, st);

@@ -52,7 +52,9 @@ struct SearchArgs {
     unsigned long long *debug;    // optional [n_warps][8] progress records
     int32_t steal;
     int32_t n_warps;
-    int32_t max_words;
+    int32_t max_words;    // bitset limit: level sets of more than 64 * max_words vertices use sorted lists
+    int32_t lbuf_cap;     // entries of the scratch list for a wide node's L' (the largest U degree)
+    int32_t lists;        // 1: some root exceeds the bitset limit (launch the variant with the list path)
 
     // outputs
     unsigned long long *totals;   // [8]: count, hash, nodes, bytes, donations, steals, -, -
@@ -79,33 +81,56 @@ enum : int32_t {
 };
 
 // Bytes of a worker's scratch region (top of its arena) for lists of
-// `ncap` candidates and root-universe rows of `urow_bytes`; the kernel lays
-// the region out in the same order: five int32 lists, two uint64 key lists,
-// the L' position list (2048 entries), the Q' mask, its word offsets and its
-// compress masks (one entry per 64 candidates), then the universe rows.
-inline int64_t scratch_layout_bytes(int64_t ncap, int64_t urow_bytes)
+// `ncap` candidates, root-universe rows of `urow_bytes` and a list of `dmax`
+// ids (L' of a node wider than the bitset limit); the kernels lay the region
+// out in the same order: five int32 lists, two uint64 key lists, then
+// (column layout only) the L' position list (2048 entries), the Q' mask, its
+// word offsets and its compress masks (one entry per 64 candidates), then
+// the universe rows, and after them the wide L' list.
+inline int64_t scratch_layout_bytes(int64_t ncap, int64_t urow_bytes, int64_t dmax)
 {
     auto p16 = [](int64_t b) { return (b + 15) / 16 * 16; };
     const int64_t qw = (ncap + 63) / 64 + 1;
-    const int64_t b =
-        5 * p16(4 * ncap) + 2 * p16(8 * ncap) + p16(4 * 2048) + p16(8 * qw) + p16(4 * qw) + p16(56 * qw) + urow_bytes + 256;
+    const int64_t b = 5 * p16(4 * ncap) + 2 * p16(8 * ncap) + p16(4 * 2048) + p16(8 * qw) + p16(4 * qw) +
+                      p16(56 * qw) + urow_bytes + p16(4 * dmax) + 256;
     return (b + 255) / 256 * 256;
 }
 
 // Bytes of a search frame's header.
 constexpr int64_t kFrameHdrBytes = 80;
 
-// Upper bound of the level-1 frame of a root of degree d with at most nc
-// candidates: header, L ids, X columns (d x ceil(nc/64) words), P ids,
-// P rows (32-row tiles of ceil(d/64) words), R ids.
+// Widest level set held as bitsets (64-bit words per row); wider level
+// sets are held as sorted id lists.
+constexpr int kMaxBitsetWords = 32;
+
+// Upper bound of the largest frame below a root of degree d with at most nc
+// candidates. A bitset frame (level set of w <= 64 * kMaxBitsetWords
+// vertices): header, L ids, X columns (w x ceil(nc/64) words), P ids, P
+// rows (32-row tiles of ceil(w/64) words), R ids. A list frame (a wider
+// level set): header, L ids, Q ids, P ids, R ids.
 #if defined(__CUDACC__)
 __host__ __device__
 #endif
 inline int64_t level1_frame_bound(int64_t d, int64_t nc)
 {
+    auto p16 = [](int64_t b) { return (b + 15) / 16 * 16; };
+    const int64_t w = d < 64 * kMaxBitsetWords ? d : 64 * kMaxBitsetWords;
+    const int64_t W = (w + 63) / 64;
+    const int64_t bits = kFrameHdrBytes + p16(4 * w) + p16(8 * w * ((nc + 63) / 64)) + p16(4 * nc) +
+                         256 * W * ((nc + 31) / 32) + p16(4 * (nc + 1));
+    const int64_t list = kFrameHdrBytes + p16(4 * d) + 2 * p16(4 * nc) + p16(4 * (nc + 1));
+    return d > w && list > bits ? list : bits;
+}
+
+// Upper bound of the root-universe rows of a root of degree d with at most
+// nc candidates (bitset rows of at most kMaxBitsetWords words).
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline int64_t universe_rows_bound(int64_t d, int64_t nc)
+{
     const int64_t W = (d + 63) / 64;
-    return kFrameHdrBytes + (4 * d + 15) / 16 * 16 + (8 * d * ((nc + 63) / 64) + 15) / 16 * 16 + (4 * nc + 15) / 16 * 16 +
-           256 * W * ((nc + 31) / 32) + (4 * (nc + 1) + 15) / 16 * 16;
+    return 256 * (W < kMaxBitsetWords ? W : kMaxBitsetWords) * ((nc + 31) / 32);
 }
 
 // Launch the persistent search kernel on stream (grid = blocks, block = threads).
@@ -114,15 +139,23 @@ cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStre
 // Bytes of per-warp shared memory the search kernel uses.
 int search_smem_per_warp();
 
+// The column-layout kernel's variant with the sorted-list path
+// (mbe_search_lists.cu); launch_search dispatches to it when args.lists.
+cudaError_t launch_search_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
+int search_lists_fit_shape(int threads, int blocks_per_sm_req);
+
 // Resident blocks per SM for a block of `threads` threads, at most
 // blocks_per_sm_req; a negative value -t means `threads` exceeds the
 // kernel's limit and t is the largest allowed block size.
 int search_fit_shape(int threads, int blocks_per_sm_req);
 
-// The same three for the row-layout search kernel (mbe_search_rows.cu).
+// The same three for the row-layout search kernel (mbe_search_rows.cu),
+// and its list-path variant (mbe_search_rows_lists.cu).
 cudaError_t launch_search_rows(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
 int search_rows_smem_per_warp();
 int search_rows_fit_shape(int threads, int blocks_per_sm_req);
+cudaError_t launch_search_rows_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
+int search_rows_lists_fit_shape(int threads, int blocks_per_sm_req);
 
 // Frame layouts of the two search kernels.
 enum : int32_t { kLayoutAuto = 0, kLayoutRows = 1, kLayoutColumns = 2 };

@@ -114,7 +114,8 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     used += align256(sizeof(int32_t) * (size_t)(max_deg + 1));
     const int64_t ncap = std::max<int64_t>(nc_max + 1, 32);
     const int64_t urow = (int64_t)align256((size_t)std::max<int64_t>(urow_max, 256));
-    const int64_t scratch = scratch_layout_bytes(ncap, urow);
+    const int32_t dmax = std::max<int32_t>(max_deg, 32);
+    const int64_t scratch = scratch_layout_bytes(ncap, urow, dmax);
     const int64_t slot = (int64_t)align256((size_t)std::max<int64_t>(frame_max, 4096));
     const int64_t mark_stride = (nU + 63) / 64 * 64;
     const int64_t min_stack = (int64_t)align256((size_t)(2 * frame_max + (256 << 10)));
@@ -175,6 +176,7 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     a.mark_stride = mark_stride;
     a.n_cand_cap = ncap;
     a.urow_bytes = urow;
+    a.lbuf_cap = dmax;
     a.cursor = &ctl->cursor;
     a.n_idle = &ctl->n_idle;
     a.outstanding = &ctl->outstanding;
@@ -185,7 +187,8 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     a.debug = nullptr;
     a.steal = 1;
     a.n_warps = n_warps;
-    a.max_words = 32;
+    a.max_words = kMaxBitsetWords;
+    a.lists = max_deg > 64 * kMaxBitsetWords ? 1 : 0;
     a.totals = ctl->totals;
     a.per_task_owner = nullptr;
     a.per_root_mode = 1;

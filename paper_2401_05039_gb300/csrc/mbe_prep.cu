@@ -103,9 +103,7 @@ __global__ void root_bounds_kernel(const GraphDesc *graphs, int32_t n_graphs, co
             s += v_off[w + 1] - v_off[w] - 1;
         }
         long long nc = s < (long long)G.nU - 1 ? s : (long long)G.nU - 1;
-        long long W = (d + 63) / 64;
-        long long tiles = (nc + 31) / 32;
-        unsigned long long urow = 256ULL * W * tiles;
+        unsigned long long urow = (unsigned long long)universe_rows_bound(d, nc);
         unsigned long long frame = (unsigned long long)level1_frame_bound(d, nc);
         m_nc = max(m_nc, (unsigned long long)nc);
         m_urow = max(m_urow, urow);
@@ -248,8 +246,7 @@ __global__ void graph_bounds_kernel(const GraphDesc *graphs, const int32_t *u_of
             s += v_off[w + 1] - v_off[w] - 1;
         }
         long long nc = s < (long long)G.nU - 1 ? s : (long long)G.nU - 1;
-        long long W = (d + 63) / 64, tiles = (nc + 31) / 32;
-        unsigned long long urow = 256ULL * W * tiles;
+        unsigned long long urow = (unsigned long long)universe_rows_bound(d, nc);
         unsigned long long frame = (unsigned long long)level1_frame_bound(d, nc);
         m_nc = max(m_nc, (unsigned long long)nc);
         m_urow = max(m_urow, urow);

@@ -33,6 +33,7 @@ struct Workspace {
     int threads = 0, blocks = 0;
     Ctl *ctl = nullptr;
     int64_t n_cand_cap = 0, urow_bytes = 0;
+    int32_t lbuf_cap = 0; // entries of the wide-node L' list in the scratch split
     bool marks_dirty = false;
     bool budget_limited = false; // fewer warps than requested because of device memory
 
@@ -66,6 +67,7 @@ struct RunInput {
     int64_t n_owner;
     int32_t per_mode;
     int32_t layout = kLayoutColumns; // resolved frame layout (kLayoutRows / kLayoutColumns)
+    int32_t max_deg = 0;             // largest U degree of the graphs searched
 };
 
 
@@ -84,7 +86,7 @@ LaunchShape shape_for(int block_threads, int blocks_per_sm, int layout);
 LaunchShape choose_shape(const mbe_options &o, int layout);
 cudaError_t launch_layout(const SearchArgs &a, int blocks, const LaunchShape &shape, cudaStream_t s);
 int ensure_workspace(Workspace &ws, int64_t nc_max, int64_t urow_max, int64_t frame_max, int32_t max_nU,
-                     const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor);
+                     const LaunchShape &shape, int64_t stack_bytes_req, int stack_factor, int32_t max_deg);
 int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStream_t s, mbe_result *out,
                mbe_biclique_buffer *bic);
 

@@ -40,6 +40,19 @@
 #include "mbe_emit.cuh"
 #include "mbe_internal.h"
 
+// MBE_LIST_PATH = 1 builds the variant with the sorted-list path for level
+// sets wider than the bitset limit (mbe_search_lists.cu); it is launched only
+// for graphs with such roots. The list path's out-of-line calls would cost
+// the plain variant registers, hence two translation units.
+#ifndef MBE_LIST_PATH
+#define MBE_LIST_PATH 0
+#endif
+#if MBE_LIST_PATH
+#define MBE_SEARCH_KERNEL search_lists_kernel
+#else
+#define MBE_SEARCH_KERNEL search_kernel
+#endif
+
 namespace mbe {
 namespace {
 
@@ -849,10 +862,9 @@ __device__ __forceinline__ void or_bits32(uint64_t *col, int p, uint32_t v)
 // pos[k] or k) into ncols column bitsets of QWd words, writing the rows as
 // bits bit0 .. bit0+n-1 of every column (OR into zeroed columns). Each
 // 32-row x 64-column block is two warp transposes.
-__device__ void rows_to_columns(Ctx &c, const uint64_t *rows, int Wr, const int32_t *pos, int n, int ncols,
+__device__ void rows_to_columns(int lane, const uint64_t *rows, int Wr, const int32_t *pos, int n, int ncols,
                                 uint64_t *cols, int QWd, int bit0)
 {
-    const int lane = c.lane;
     for (int t0 = 0; t0 < n; t0 += 32) {
         const int k = t0 + lane;
         const bool valid = k < n;
@@ -1043,7 +1055,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         q_copy_columns(c, F.Q, QW, LW, last, J, mp, D.Q, QWd);
     }
     const uint64_t t_tr = tnow(a);
-    rows_to_columns(c, D.rows, Wd, nullptr, pn, mp, D.Q, QWd, qposd);
+    rows_to_columns(lane, D.rows, Wd, nullptr, pn, mp, D.Q, QWd, qposd);
     if (lane == 0 && c.dbg) {
         const uint64_t now = globaltimer();
         c.dbg[23] += now - t_qc;
@@ -1077,11 +1089,116 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     return cp;
 }
 
+// ------------------------------------------------------ wide level sets
+#include "mbe_list.cuh"
+
+// A bitset child of a list node (mbe_list.cuh) in the column layout. One
+// reverse scan over L' sets bit j of the universe row of every member of
+// Q' u P' adjacent to L'[j]; the rows of P' are copied into the frame, and
+// Q' and P' are transposed into its columns.
+__device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv &e, char *cp, const GView &G,
+                                              int graph, int root, int depth, int64_t parent, const int32_t *Lp,
+                                              int mp, const int32_t *Qg, int nQd, const uint64_t *Pk, int pn,
+                                              uint64_t Rs, const int32_t *Ra, int na, const int32_t *Rb, int nb)
+{
+    const int lane = e.lane;
+    const int W = (mp + 63) >> 6, n = nQd + pn;
+    const int64_t tiles = (n + 31) >> 5;
+    const int QW = (n + 63) >> 6;
+    const int nRd = a.emit ? na + nb : 0;
+    const int64_t sz = frame_bytes(mp, QW, pn, W, nRd);
+    if (n > e.ncap || tiles * W * 32 > e.urow_words || ((uintptr_t)cp & 15) || cp + sz > e.limit) {
+        if (lane == 0) set_error(a, kErrArena);
+        return nullptr;
+    }
+    const uint64_t id_mask = (1ULL << a.key_shift) - 1;
+    for (int k = lane; k < n; k += 32) {
+        const int u = k < nQd ? Qg[k] : (int32_t)(Pk[k - nQd] & id_mask);
+        e.mark[u] = k;
+        e.ugid[k] = u;
+    }
+    for (int64_t k = lane; k < tiles * W * 32; k += 32) e.urows[k] = 0;
+    __syncwarp();
+    uint64_t *urows = e.urows;
+    reverse_scan(lane, G, Lp, mp, e.mark, [&](int k, int j) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&urows[row_word(k, j >> 6, W)]), 1ULL << (j & 63));
+    });
+    for (int k = lane; k < n; k += 32) e.mark[e.ugid[k]] = -1;
+    Frame D = frame_at(cp, mp, QW, pn, W);
+    for (int k = lane; k < pn; k += 32) D.gid[k] = e.ugid[nQd + k];
+    for (int k = lane; k < mp; k += 32) D.Lid[k] = Lp[k];
+    for (int64_t t = lane; t < (int64_t)pn * W; t += 32) {
+        const int k = (int)(t / W), w = (int)(t - (int64_t)k * W);
+        D.rows[row_word(k, w, W)] = urows[row_word(nQd + k, w, W)];
+    }
+    for (int64_t k = lane; k < (int64_t)mp * QW; k += 32) D.Q[k] = 0;
+    __syncwarp();
+    if (nQd > 0) rows_to_columns(lane, urows, W, nullptr, nQd, mp, D.Q, QW, 0);
+    rows_to_columns(lane, D.rows, W, nullptr, pn, mp, D.Q, QW, nQd);
+    if (a.emit) emit::merge_into(lane, Ra, na, Rb, nb, D.R);
+    if (lane == 0) {
+        FrameHdr h;
+        h.m = mp;
+        h.W = W;
+        h.nQ = nQd;
+        h.nP = pn;
+        h.i = 0;
+        h.end = pn;
+        h.root = root;
+        h.graph = graph;
+        h.Rsum = Rs;
+        h.nR = nRd;
+        h.QW = QW;
+        h.bytes = sz;
+        h.parent = parent;
+        h.qpos = nQd;
+        h.copy_hint = 1;
+        h.pad_[0] = h.pad_[1] = 0;
+        *D.h = h;
+    }
+    __syncwarp();
+    return cp;
+}
+
+// The list path's view of a worker.
+__device__ __forceinline__ ListEnv list_env(const Ctx &c)
+{
+    ListEnv e;
+    e.lane = c.lane;
+    e.mark = c.mark;
+    e.hist = c.hist;
+    e.arena = c.arena;
+    e.limit = c.limit;
+    e.qsrc = c.s.qsrc;
+    e.psrc = c.s.psrc;
+    e.psrc2 = c.s.psrc2;
+    e.rtmp = c.s.rtmp;
+    e.ugid = c.s.ugid;
+    e.lbuf = reinterpret_cast<int32_t *>(c.s.urows + c.s.urow_words); // after the universe rows
+    e.pkey = c.s.pkey;
+    e.pkey2 = c.s.pkey2;
+    e.urows = c.s.urows;
+    e.ncap = c.s.ncap;
+    e.urow_words = c.s.urow_words;
+    return e;
+}
+
+__device__ __forceinline__ char *take_list_out(Ctx &c, const ListOut &o)
+{
+    c.cnt += o.cnt;
+    c.hash += o.hash;
+    c.bytes += o.bytes;
+    if (o.abort) c.abort = true;
+    return o.child;
+}
+
 // ------------------------------------------------------------- root task
 // The top-level iteration for candidate r: L' = N(r), the root-local
 // universe of N2(r), the check against the earlier-ranked candidates, the
 // expansion by the later-ranked ones, and the level-1 frame at the bottom
 // of the stack. Returns true when a frame was pushed.
+constexpr bool kLists = MBE_LIST_PATH != 0;
+
 __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r, int graph, int part, int parts)
 {
     const int lane = c.lane;
@@ -1094,10 +1211,14 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     if (first) c.nodes += 1;
     if (d == 0) return false;
     const int W = (d + 63) >> 6;
-    if (W > a.max_words) {
-        if (lane == 0) set_error(a, kErrUnsupported);
-        c.abort = true;
-        return false;
+    if (W > a.max_words) { // a sorted-list level set
+        if constexpr (kLists) {
+            return take_list_out(c, list_root(a, list_env(c), G, r, graph, part, parts)) != nullptr;
+        } else {
+            if (lane == 0) set_error(a, kErrInternal); // the host launches the list variant for such graphs
+            c.abort = true;
+            return false;
+        }
     }
     Scratch &S = c.s;
     int32_t *mark = c.mark;
@@ -1305,8 +1426,8 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     // X = the earlier-ranked candidates, then P in pop order, transposed
     // into one column per vertex of N(r)
     zero_words(c, D.Q, (int64_t)d * QW);
-    if (qn > 0) rows_to_columns(c, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
-    rows_to_columns(c, D.rows, W, nullptr, pn, d, D.Q, QW, qn);
+    if (qn > 0) rows_to_columns(lane, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
+    rows_to_columns(lane, D.rows, W, nullptr, pn, d, D.Q, QW, qn);
     if (a.emit)
         for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {
@@ -1515,7 +1636,17 @@ __device__ void run_stack(const SearchArgs &a, Ctx &c, char *top)
             }
             if (a.steal) maybe_donate(a, c, top);
         }
-        char *child = process_node(a, c, top);
+        char *child;
+        if constexpr (kLists) {
+            if (is_list_frame(top)) {
+                c.nodes += 1;
+                child = take_list_out(c, list_node(a, list_env(c), top));
+            } else {
+                child = process_node(a, c, top);
+            }
+        } else {
+            child = process_node(a, c, top);
+        }
         __syncwarp(); // header updates by lane 0 are visible to the whole warp
         if (child) {
             top = child;
@@ -1548,7 +1679,7 @@ __device__ void finish_task(const SearchArgs &a, Ctx &c, int owner)
 #ifndef MBE_SEARCH_MIN_BLOCKS
 #define MBE_SEARCH_MIN_BLOCKS 2 // resident 256-thread blocks per SM the register budget is sized for
 #endif
-__global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(SearchArgs a)
+__global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) MBE_SEARCH_KERNEL(SearchArgs a)
 {
     extern __shared__ uint32_t smem[];
     Ctx c;
@@ -1626,7 +1757,10 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(Sear
         }
         t = __shfl_sync(kFull, t, 0);
         if (t >= 0) {
-            if (idle && c.lane == 0) atomicSub(a.n_idle, 1);
+            if (idle && c.lane == 0) {
+                atomicSub(a.n_idle, 1);
+                if (c.dbg) c.dbg[29] += globaltimer() - idle_since; // idle between tasks
+            }
             idle = false;
             int g = a.task_graph ? a.task_graph[t] : 0;
             int r = a.task_root[t];
@@ -1644,12 +1778,16 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(Sear
                 if (c.dbg) c.dbg[14] += 1;
             }
             finish_task(a, c, a.per_root_mode == 2 ? g : r);
+            if (c.lane == 0 && c.dbg) c.dbg[28] = globaltimer() - c.t_start; // end of the last task
             if (c.abort) break;
             continue;
         }
         // 2) a published frame (own slot first)
         if (a.steal && try_steal(a, c)) {
-            if (idle && c.lane == 0) atomicSub(a.n_idle, 1);
+            if (idle && c.lane == 0) {
+                atomicSub(a.n_idle, 1);
+                if (c.dbg) c.dbg[29] += globaltimer() - idle_since; // idle between tasks
+            }
             idle = false;
             const FrameHdr *h = reinterpret_cast<const FrameHdr *>(c.arena);
             int owner = a.per_root_mode == 2 ? h->graph : h->root;
@@ -1663,6 +1801,7 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(Sear
                 if (c.dbg) c.dbg[15] += 1;
             }
             finish_task(a, c, owner);
+            if (c.lane == 0 && c.dbg) c.dbg[28] = globaltimer() - c.t_start; // end of the last task
             if (c.abort) break;
             continue;
         }
@@ -1715,6 +1854,38 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) search_kernel(Sear
 
 } // namespace
 
+#if MBE_LIST_PATH
+
+int search_lists_fit_shape(int threads, int blocks_per_sm_req)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, MBE_SEARCH_KERNEL) != cudaSuccess) return 0;
+    if (threads > fa.maxThreadsPerBlock) return -fa.maxThreadsPerBlock / 32 * 32;
+    const int smem = (threads / 32) * kSmemWords * 4;
+    cudaFuncSetAttribute(MBE_SEARCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kSmemWords * 4);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, MBE_SEARCH_KERNEL, threads, smem) != cudaSuccess) return 0;
+    return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
+}
+
+cudaError_t launch_search_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
+{
+    static int smem_set[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int smem = (threads / 32) * kSmemWords * 4;
+    if (dev >= 0 && dev < 64 && smem_set[dev] < 32 * kSmemWords * 4) {
+        cudaError_t e =
+            cudaFuncSetAttribute(MBE_SEARCH_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kSmemWords * 4);
+        if (e != cudaSuccess) return e;
+        smem_set[dev] = 32 * kSmemWords * 4;
+    }
+    MBE_SEARCH_KERNEL<<<blocks, threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+#else
+
 int search_smem_per_warp() { return kSmemWords * 4; }
 
 int search_fit_shape(int threads, int blocks_per_sm_req)
@@ -1728,11 +1899,16 @@ int search_fit_shape(int threads, int blocks_per_sm_req)
     cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * search_smem_per_warp());
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, threads, smem) != cudaSuccess) return 0;
+    // the list variant must fit the same shape
+    const int per_sm_l = search_lists_fit_shape(threads, per_sm);
+    if (per_sm_l <= 0) return per_sm_l;
+    if (per_sm_l < per_sm) per_sm = per_sm_l;
     return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
 }
 
 cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
 {
+    if (a.lists) return launch_search_lists(a, blocks, threads, stream);
     // the dynamic shared memory limit is raised once to the largest block
     // (no attribute calls between captured launches)
     static int smem_set[64] = {0};
@@ -1748,5 +1924,7 @@ cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStre
     search_kernel<<<blocks, threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
+
+#endif
 
 } // namespace mbe

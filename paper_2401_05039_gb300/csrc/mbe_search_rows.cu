@@ -35,6 +35,18 @@
 #include "mbe_emit.cuh"
 #include "mbe_internal.h"
 
+// MBE_LIST_PATH = 1 builds the variant with the sorted-list path for level
+// sets wider than the bitset limit (mbe_search_rows_lists.cu); it is launched
+// only for graphs with such roots.
+#ifndef MBE_LIST_PATH
+#define MBE_LIST_PATH 0
+#endif
+#if MBE_LIST_PATH
+#define MBE_ROWS_KERNEL search_rows_lists_kernel
+#else
+#define MBE_ROWS_KERNEL search_rows_kernel
+#endif
+
 namespace mbe {
 namespace {
 
@@ -639,6 +651,98 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     return cp;
 }
 
+// ------------------------------------------------------ wide level sets
+#include "mbe_list.cuh"
+
+// A bitset child of a list node (mbe_list.cuh) in the row layout: one
+// reverse scan over L' sets bit j of the row of every member of Q' u P'
+// adjacent to L'[j], directly in the frame's [Q' | P'] rows.
+__device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv &e, char *cp, const GView &G,
+                                              int graph, int root, int depth, int64_t parent, const int32_t *Lp,
+                                              int mp, const int32_t *Qg, int nQd, const uint64_t *Pk, int pn,
+                                              uint64_t Rs, const int32_t *Ra, int na, const int32_t *Rb, int nb)
+{
+    const int lane = e.lane;
+    const int W = (mp + 63) >> 6, n = nQd + pn;
+    const int64_t tiles = (n + 31) >> 5;
+    const int nRd = a.emit ? na + nb : 0;
+    const int64_t sz = frame_bytes(mp, n, W, nRd);
+    if (n > e.ncap || ((uintptr_t)cp & 15) || cp + sz > e.limit) {
+        if (lane == 0) set_error(a, kErrArena);
+        return nullptr;
+    }
+    const uint64_t id_mask = (1ULL << a.key_shift) - 1;
+    Frame D = frame_at(cp, mp, n, W);
+    for (int k = lane; k < n; k += 32) {
+        const int u = k < nQd ? Qg[k] : (int32_t)(Pk[k - nQd] & id_mask);
+        e.mark[u] = k;
+        D.gid[k] = u;
+    }
+    for (int k = lane; k < mp; k += 32) D.Lid[k] = Lp[k];
+    for (int64_t k = lane; k < tiles * W * 32; k += 32) D.rows[k] = 0;
+    __syncwarp();
+    uint64_t *rows = D.rows;
+    reverse_scan(lane, G, Lp, mp, e.mark, [&](int k, int j) {
+        atomicOr(reinterpret_cast<unsigned long long *>(&rows[row_word(k, j >> 6, W)]), 1ULL << (j & 63));
+    });
+    for (int k = lane; k < n; k += 32) e.mark[D.gid[k]] = -1;
+    if (a.emit) emit::merge_into(lane, Ra, na, Rb, nb, D.R);
+    __syncwarp();
+    if (lane == 0) {
+        FrameHdr h;
+        h.m = mp;
+        h.W = W;
+        h.nQ = nQd;
+        h.nP = pn;
+        h.i = 0;
+        h.end = pn;
+        h.root = root;
+        h.graph = graph;
+        h.Rsum = Rs;
+        h.nR = nRd;
+        h.depth = depth;
+        h.bytes = sz;
+        h.parent = parent;
+        *D.h = h;
+    }
+    __syncwarp();
+    return cp;
+}
+
+// The list path's view of a worker.
+__device__ __forceinline__ ListEnv list_env(const Ctx &c)
+{
+    ListEnv e;
+    e.lane = c.lane;
+    e.mark = c.mark;
+    e.hist = c.hist;
+    e.arena = c.arena;
+    e.limit = c.limit;
+    e.qsrc = c.s.qsrc;
+    e.psrc = c.s.psrc;
+    e.psrc2 = c.s.psrc2;
+    e.rtmp = c.s.rtmp;
+    e.ugid = c.s.ugid;
+    e.lbuf = reinterpret_cast<int32_t *>(c.s.urows + c.s.urow_words); // after the universe rows
+    e.pkey = c.s.pkey;
+    e.pkey2 = c.s.pkey2;
+    e.urows = c.s.urows;
+    e.ncap = c.s.ncap;
+    e.urow_words = c.s.urow_words;
+    return e;
+}
+
+__device__ __forceinline__ char *take_list_out(Ctx &c, const ListOut &o)
+{
+    c.cnt += o.cnt;
+    c.hash += o.hash;
+    c.bytes += o.bytes;
+    if (o.abort) c.abort = true;
+    return o.child;
+}
+
+constexpr bool kLists = MBE_LIST_PATH != 0;
+
 // ------------------------------------------------------------- root task
 // The top-level iteration for candidate r: L' = N(r), the root-local
 // universe of N2(r), the check against the earlier-ranked candidates, the
@@ -656,10 +760,14 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     if (first) c.nodes += 1;
     if (d == 0) return false;
     const int W = (d + 63) >> 6;
-    if (W > a.max_words) {
-        if (lane == 0) set_error(a, kErrUnsupported);
-        c.abort = true;
-        return false;
+    if (W > a.max_words) { // a sorted-list level set
+        if constexpr (kLists) {
+            return take_list_out(c, list_root(a, list_env(c), G, r, graph, part, parts)) != nullptr;
+        } else {
+            if (lane == 0) set_error(a, kErrInternal); // the host launches the list variant for such graphs
+            c.abort = true;
+            return false;
+        }
     }
     Scratch &S = c.s;
     int32_t *mark = c.mark;
@@ -1024,7 +1132,17 @@ __device__ void run_stack(const SearchArgs &a, Ctx &c, char *top)
             }
             if (a.steal) maybe_donate(a, c, top);
         }
-        char *child = process_node(a, c, top);
+        char *child;
+        if constexpr (kLists) {
+            if (is_list_frame(top)) {
+                c.nodes += 1;
+                child = take_list_out(c, list_node(a, list_env(c), top));
+            } else {
+                child = process_node(a, c, top);
+            }
+        } else {
+            child = process_node(a, c, top);
+        }
         __syncwarp(); // header updates by lane 0 are visible to the whole warp
         if (child) {
             top = child;
@@ -1054,7 +1172,7 @@ __device__ void finish_task(const SearchArgs &a, Ctx &c, int owner)
     __syncwarp();
 }
 
-__global__ void __launch_bounds__(256, 2) search_rows_kernel(SearchArgs a)
+__global__ void __launch_bounds__(256, 2) MBE_ROWS_KERNEL(SearchArgs a)
 {
     extern __shared__ uint32_t smem[];
     Ctx c;
@@ -1122,7 +1240,10 @@ __global__ void __launch_bounds__(256, 2) search_rows_kernel(SearchArgs a)
         }
         t = __shfl_sync(kFull, t, 0);
         if (t >= 0) {
-            if (idle && c.lane == 0) atomicSub(a.n_idle, 1);
+            if (idle && c.lane == 0) {
+                atomicSub(a.n_idle, 1);
+                if (c.dbg) c.dbg[29] += globaltimer() - idle_since; // idle between tasks
+            }
             idle = false;
             int g = a.task_graph ? a.task_graph[t] : 0;
             int r = a.task_root[t];
@@ -1140,12 +1261,16 @@ __global__ void __launch_bounds__(256, 2) search_rows_kernel(SearchArgs a)
                 if (c.dbg) c.dbg[14] += 1;
             }
             finish_task(a, c, a.per_root_mode == 2 ? g : r);
+            if (c.lane == 0 && c.dbg) c.dbg[28] = globaltimer() - c.t_start; // end of the last task
             if (c.abort) break;
             continue;
         }
         // 2) a published frame (own slot first)
         if (a.steal && try_steal(a, c)) {
-            if (idle && c.lane == 0) atomicSub(a.n_idle, 1);
+            if (idle && c.lane == 0) {
+                atomicSub(a.n_idle, 1);
+                if (c.dbg) c.dbg[29] += globaltimer() - idle_since; // idle between tasks
+            }
             idle = false;
             const FrameHdr *h = reinterpret_cast<const FrameHdr *>(c.arena);
             int owner = a.per_root_mode == 2 ? h->graph : h->root;
@@ -1159,6 +1284,7 @@ __global__ void __launch_bounds__(256, 2) search_rows_kernel(SearchArgs a)
                 if (c.dbg) c.dbg[15] += 1;
             }
             finish_task(a, c, owner);
+            if (c.lane == 0 && c.dbg) c.dbg[28] = globaltimer() - c.t_start; // end of the last task
             if (c.abort) break;
             continue;
         }
@@ -1211,6 +1337,38 @@ __global__ void __launch_bounds__(256, 2) search_rows_kernel(SearchArgs a)
 
 } // namespace
 
+#if MBE_LIST_PATH
+
+int search_rows_lists_fit_shape(int threads, int blocks_per_sm_req)
+{
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, MBE_ROWS_KERNEL) != cudaSuccess) return 0;
+    if (threads > fa.maxThreadsPerBlock) return -fa.maxThreadsPerBlock / 32 * 32;
+    const int smem = (threads / 32) * kSmemWords * 4;
+    cudaFuncSetAttribute(MBE_ROWS_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kSmemWords * 4);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, MBE_ROWS_KERNEL, threads, smem) != cudaSuccess) return 0;
+    return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
+}
+
+cudaError_t launch_search_rows_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
+{
+    static int smem_set[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const int smem = (threads / 32) * kSmemWords * 4;
+    if (dev >= 0 && dev < 64 && smem_set[dev] < 32 * kSmemWords * 4) {
+        cudaError_t e =
+            cudaFuncSetAttribute(MBE_ROWS_KERNEL, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * kSmemWords * 4);
+        if (e != cudaSuccess) return e;
+        smem_set[dev] = 32 * kSmemWords * 4;
+    }
+    MBE_ROWS_KERNEL<<<blocks, threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+#else
+
 int search_rows_smem_per_warp() { return kSmemWords * 4; }
 
 int search_rows_fit_shape(int threads, int blocks_per_sm_req)
@@ -1226,11 +1384,16 @@ int search_rows_fit_shape(int threads, int blocks_per_sm_req)
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_rows_kernel, threads, smem) != cudaSuccess)
         return 0;
+    // the list variant must fit the same shape
+    const int per_sm_l = search_rows_lists_fit_shape(threads, per_sm);
+    if (per_sm_l <= 0) return per_sm_l;
+    if (per_sm_l < per_sm) per_sm = per_sm_l;
     return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
 }
 
 cudaError_t launch_search_rows(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
 {
+    if (a.lists) return launch_search_rows_lists(a, blocks, threads, stream);
     // the dynamic shared memory limit is raised once to the largest block
     // (no attribute calls between captured launches)
     static int smem_set[64] = {0};
@@ -1246,5 +1409,7 @@ cudaError_t launch_search_rows(const SearchArgs &a, int blocks, int threads, cud
     search_rows_kernel<<<blocks, threads, smem, stream>>>(a);
     return cudaGetLastError();
 }
+
+#endif
 
 } // namespace mbe

@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
 class ClassParams(ctypes.Structure):
     _fields_ = [("block_threads", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("steal", ctypes.c_int32),
                 ("valid", ctypes.c_int32), ("layout", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("tuned_ms", ctypes.c_double)]
+                ("tuned_ms", ctypes.c_double), ("default_ms", ctypes.c_double)]
 
 
 N_CLASSES = 8
@@ -440,8 +440,55 @@ def allreduce_totals(totals, group=None):
     return tuple(out)
 
 
-def sharded_enumerate(graph, rank: int, world: int, n_roots: int, group=None, **kw):
-    """Rank's shard of graph's execution order (n_roots = its length), summed over the group."""
-    b, e = shard_bounds(n_roots, rank, world)
-    r = graph.enumerate(root_begin=b, root_end=e, **kw)
+def lpt_shards(cost, world: int):
+    """Roots assigned to `world` ranks, longest processing time first.
+
+    cost[u] is the expected cost of root u (a prediction of the cost network
+    or a static proxy); roots with cost <= 0 (isolated vertices) are left
+    out. Roots are taken in descending cost and each goes to the rank with
+    the least load so far, so the largest load is at most 4/3 of the best
+    possible. Returns one int32 array of root ids per rank, in descending
+    cost (the order in which that rank should run them).
+    """
+    import heapq
+    if world < 1:
+        raise ValueError("need world >= 1")
+    cost = np.asarray(cost, dtype=np.float64)
+    ids = np.nonzero(cost > 0)[0]
+    order = ids[np.argsort(-cost[ids], kind="stable")]
+    heap = [(0.0, r) for r in range(world)]
+    out = [[] for _ in range(world)]
+    for u in order.tolist():
+        load, r = heapq.heappop(heap)
+        out[r].append(u)
+        heapq.heappush(heap, (load + float(cost[u]), r))
+    return [np.asarray(o, dtype=np.int32) for o in out]
+
+
+def static_root_cost(raw_features):
+    """Static cost proxy of every root from mbe_root_features' raw values.
+
+    The number of (neighbour, second neighbour) pairs the root's setup reads
+    (sum of the degrees of N(r)) times its candidate count |N2(r)|; zero for
+    isolated roots.
+    """
+    raw = np.asarray(raw_features, dtype=np.float64)
+    return raw[:, 5] * np.maximum(raw[:, 1], 1.0) * (raw[:, 0] > 0)
+
+
+def sharded_enumerate(graph, rank: int, world: int, n_roots: int = 0, group=None, cost=None, **kw):
+    """Rank's shard of the graph's roots, enumerated on this rank's GPU and summed over the group.
+
+    Without `cost`: the contiguous equal-count share [begin, end) of the
+    static execution order (n_roots = its length). With `cost` (per root id):
+    the rank's LPT share (lpt_shards), run as an explicit execution order.
+    """
+    if cost is None:
+        b, e = shard_bounds(n_roots, rank, world)
+        r = graph.enumerate(root_begin=b, root_end=e, **kw)
+    else:
+        import torch
+        mine = lpt_shards(cost, world)[rank]
+        order = torch.from_numpy(mine).cuda()
+        r = graph.enumerate(exec_order=order, n_exec=int(mine.shape[0]), **kw)
     return allreduce_totals((r.count, r.hash, r.nodes, r.bytes_alg), group)

@@ -58,8 +58,9 @@ int main(void) {{
          offsetof(mbe_options, per_root), offsetof(mbe_options, n_exec));
   printf("%zu %zu %zu\\n", offsetof(mbe_result, device_ms), offsetof(mbe_result, status),
          offsetof(mbe_result, n_donations));
-  printf("%zu %zu %zu %zu\\n", offsetof(mbe_options, layout), sizeof(mbe_class_params),
-         offsetof(mbe_class_params, layout), offsetof(mbe_class_params, tuned_ms));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(mbe_options, layout), sizeof(mbe_class_params),
+         offsetof(mbe_class_params, layout), offsetof(mbe_class_params, tuned_ms),
+         offsetof(mbe_class_params, default_ms));
   return 0;
 }}''')
     exe = tmp_path / "layout"
@@ -71,7 +72,7 @@ int main(void) {{
     assert vals[3:7] == [O.arena_bytes.offset, O.model.offset, O.per_root.offset, O.n_exec.offset]
     assert vals[7:10] == [R.device_ms.offset, R.status.offset, R.n_donations.offset]
     C = m.ClassParams
-    assert vals[10:14] == [O.layout.offset, ctypes.sizeof(C), C.layout.offset, C.tuned_ms.offset]
+    assert vals[10:15] == [O.layout.offset, ctypes.sizeof(C), C.layout.offset, C.tuned_ms.offset, C.default_ms.offset]
 
 
 def test_compress_helper_matches_bit_gather(tmp_path):

@@ -85,3 +85,35 @@ def test_batch_equals_single_graph_calls_and_autotune(mbe, gold, graphs):
         assert table[c].valid == 1 and table[c].block_threads > 0 and table[c].layout in (1, 2)
     per2, tot2 = mbe.enumerate_batch(b, class_params=table)
     assert [_row(p) for p in per2] == [_row(p) for p in per]
+
+
+def test_full_batch_in_one_call(mbe, gold, graphs):
+    # the 4,096-graph workload as stated, in one mbe_enumerate_batch call:
+    # every graph the oracle finished whole is exact; every other graph equals
+    # one mbe_enumerate on its own, whose per-root rows match the oracle's
+    # stored rows for that graph; per-graph device times are the class times
+    import torch
+    b = synth.pack(graphs)
+    per, tot = mbe.enumerate_batch(b)
+    assert tot.status == 0
+    for k, d in gold["per_graph"].items():
+        assert _row(per[int(k)]) == _exp(d), k
+    rest = gold["rest_graph_roots"]
+    assert len(rest) + len(gold["per_graph"]) == len(graphs)
+    for gi, rows in rest.items():
+        g = graphs[int(gi)]
+        G = mbe.Graph.from_synth(g)
+        buf = torch.zeros((g.nU, 4), dtype=torch.int64, device="cuda")
+        r = G.enumerate(per_root=buf)
+        got = buf.cpu().numpy().view(np.uint64)
+        G.close()
+        assert _row(r) == _row(per[int(gi)]), gi
+        for root, d in rows.items():
+            assert tuple(int(x) for x in got[int(root)]) == _exp(d), (gi, root)
+    assert tot.count == sum(int(p.count) for p in per)
+    assert tot.hash == sum(int(p.hash) for p in per) % (1 << 64)
+    classes = {}
+    for g, p in zip(graphs, per):
+        classes.setdefault(mbe.batch_class(g.nU, g.nV, g.nE), set()).add(round(p.device_ms, 6))
+    assert all(len(v) == 1 and min(v) > 0 for v in classes.values())
+    assert sum(min(v) for v in classes.values()) <= tot.device_ms * 1.01

@@ -314,16 +314,62 @@ def test_invalid_layout_rejected(mbe):
     G.close()
 
 
+def wide_graphs():
+    """Graphs with roots of degree above 2,048 (the widest bitset level set)."""
+    rng = np.random.default_rng(5)
+    edges = [(u, v) for u in range(3) for v in range(5000)]
+    us, vs = np.nonzero(rng.random((40, 5000)) < 0.02)
+    edges += [(3 + int(u), int(v)) for u, v in zip(us, vs)]
+    k3 = H.graph(43, 5000, edges, "K3,5000 + 40 sparse vertices")
+    rng = np.random.default_rng(6)
+    edges = [(int(u), int(v)) for u, v in zip(*np.nonzero(rng.random((5, 6000)) < 0.9))]
+    edges += [(5 + int(u), int(v)) for u, v in zip(*np.nonzero(rng.random((30, 6000)) < 0.01))]
+    hubs = H.graph(35, 6000, edges, "5 hubs sharing ~4,900 neighbours + 30 sparse vertices")
+    return [k3, hubs, H.complete(2, 2100),
+            synth.chung_lu(200, 10000, 12000, 1.8, 2.5, 8000, 7),   # one root of degree 2,694
+            synth.chung_lu(400, 15000, 20000, 1.9, 2.5, 8000, 8),   # 3,178
+            synth.chung_lu(150, 12000, 15000, 1.7, 2.6, 10000, 9)]  # 2,057 and 4,494
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
-def test_root_degree_beyond_bitset_limit_is_unsupported(mbe, layout):
-    # a root with more than 2,048 neighbours (32 words per bitset row) is
-    # outside the bitset path: the call reports MBE_ERR_UNSUPPORTED cleanly
-    # and the next call on another graph is unaffected
-    g = H.complete(2, 2100)
-    r = run(mbe, g, layout=layout, check=False)
-    assert r.status == 8
-    g2 = synth.workload("er200x300")
-    assert gpu_tuple(run(mbe, g2, layout=layout)) == oracle_tuple(g2)
+def test_wide_roots_take_the_sorted_list_path(mbe, layout):
+    # roots (and, for the hub graph, nodes two and three levels down) wider
+    # than 2,048 vertices run as sorted-list frames with reverse-scan counts;
+    # narrower children become bitset frames. Bit-exact against the oracle,
+    # including the per-root rows of the widest graph.
+    import torch
+    for g in wide_graphs():
+        assert int(np.diff(g.u_off).max()) > 2048
+        assert gpu_tuple(run(mbe, g, layout=layout)) == oracle_tuple(g), g.name
+    g = wide_graphs()[-1]
+    G = mbe.Graph.from_synth(g)
+    buf = torch.zeros((g.nU, 4), dtype=torch.int64, device="cuda")
+    G.enumerate(per_root=buf, layout=layout)
+    assert (buf.cpu().numpy().view(np.uint64) == oracle.per_root(g, nthreads=4)).all()
+    G.close()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("words", [1, 2])
+def test_bitset_limit_sweep(mbe, layout, words):
+    # a bitset limit of 64 or 128 vertices sends every wider level set of
+    # these small graphs through the list path (roots, inner nodes, list
+    # children and bitset children of list nodes): results do not change
+    import torch
+    for g in _random_cases(2000 + words, 20):
+        assert gpu_tuple(run(mbe, g, layout=layout, bitset_max_words=words)) == oracle_tuple(g), (g.nU, g.nV)
+    g = synth.workload("er200x300")
+    c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
+    G = mbe.Graph.from_synth(g)
+    buf = mbe.Bicliques.allocate(200000, 10000)
+    r = G.enumerate(emit=1, bicliques=buf.buf, layout=layout, bitset_max_words=words)
+    torch.cuda.synchronize()
+    got = raw_records(buf)
+    assert gpu_tuple(r) == (c, h, n, b)
+    assert all(ascending(R) and ascending(L) for R, L in got)
+    assert sorted(got) == sorted(rec)
+    assert gpu_tuple(G.enumerate(layout=layout, bitset_max_words=words, steal=0)) == (c, h, n, b)
+    G.close()
 
 
 def test_invalid_graphs_rejected(mbe):
