@@ -154,6 +154,7 @@ typedef struct {
     uint64_t bytes_b;      /* the second byte model, see bytes_node_b */
     const int32_t *rootL;  /* L of the current root's level-1 call, N(r), sorted */
     int64_t nRootL;
+    int32_t min_r, min_l;  /* size filter: only bicliques with |R| >= min_r and |L| >= min_l (1, 1 = all) */
 } oacc;
 
 /*
@@ -260,23 +261,27 @@ static void mbea_iteration(const ograph *g, const ovec *L, const ovec *R, int32_
     }
 
     if (is_maximal) {
-        /* Step 4: maximal expansion over the rest of P */
+        /* Step 4: maximal expansion over the rest of P. With a size filter
+           (min_l > 1) a candidate reaching fewer than min_l vertices of L'
+           does not enter P': every node it would start has |L''| < min_l. */
         for (int64_t i = 0; i < n_rest; ++i) {
             int64_t dp;
             const int32_t *Np = nbr(g, P_rest[i], &dp);
             int64_t c = count_common(Np, dp, Lp.a, Lp.n);
             if (c == Lp.n) {
                 if (ov_push(&Rp, P_rest[i])) goto oom;
-            } else if (c > 0) {
+            } else if (c > 0 && c >= acc->min_l) {
                 if (ov_push(&Pp, P_rest[i])) goto oom;
             }
         }
-        emit(acc, &Lp, &Rp);
+        if (Rp.n >= acc->min_r && Lp.n >= acc->min_l) emit(acc, &Lp, &Rp);
         if (R->n == 0) { /* x is this root: its level-1 call works inside N(x) */
             acc->rootL = Lp.a;
             acc->nRootL = Lp.n;
         }
-        if (Pp.n != 0) mbea(g, &Lp, &Rp, &Pp, &Qp, acc);
+        /* the subtree's level sets are strictly smaller than L' and its R
+           within R' u P': recurse only when some biclique there can pass */
+        if (Pp.n != 0 && Lp.n - 1 >= acc->min_l && Rp.n + Pp.n >= acc->min_r) mbea(g, &Lp, &Rp, &Pp, &Qp, acc);
     }
     if (R->n == 0) { /* top level: the root's adjacency (both byte models) */
         uint64_t b = 4ULL * (uint64_t)dx;
@@ -367,29 +372,34 @@ done:
     ov_free(&Qc);
 }
 
-/* Initial sets of the top-level call. */
-static int top_level(const ograph *g, ovec *L, ovec *P)
+/* Initial sets of the top-level call: L = V, P = the U vertices of degree at
+   least max(1, min_l) (an isolated vertex gives L' = {}; with a size filter
+   a vertex of degree below min_l is in no biclique that passes it). */
+static int top_level(const ograph *g, ovec *L, ovec *P, int32_t min_l)
 {
+    const int32_t dmin = min_l > 1 ? min_l : 1;
     for (int32_t v = 0; v < g->nV; ++v)
         if (ov_push(L, v)) return -1;
     for (int32_t u = 0; u < g->nU; ++u)
-        if (g->u_off[u + 1] > g->u_off[u] && ov_push(P, u)) return -1;
+        if (g->u_off[u + 1] - g->u_off[u] >= dmin && ov_push(P, u)) return -1;
     return 0;
 }
 
 /*
  * Whole-graph enumeration, serial. out[0..3] = count, hash, nodes, bytes;
- * *out_b (when not NULL) = bytes under the second model. When rec != NULL, *rec receives a malloc'd int32 array of records
+ * *out_b (when not NULL) = bytes under the second model. min_r, min_l: the
+ * size filter (1, 1 = every maximal biclique). When rec != NULL, *rec receives a malloc'd int32 array of records
  * (|R|, |L|, R..., L...) and *rec_len its length (free with orc_free).
  * Returns 0, or -1 on allocation failure.
  */
 int orc_enumerate(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
-                  const int32_t *v_adj, uint64_t *out, int32_t **rec, int64_t *rec_len, uint64_t *out_b)
+                  const int32_t *v_adj, uint64_t *out, int32_t **rec, int64_t *rec_len, uint64_t *out_b,
+                  int32_t min_r, int32_t min_l)
 {
     ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
     ovec L = {0}, R = {0}, P = {0}, Q = {0}, records = {0};
-    oacc acc = {0, 0, 0, 0, rec ? &records : NULL, 0, 0, NULL, 0};
-    if (top_level(&g, &L, &P)) acc.err = 1;
+    oacc acc = {0, 0, 0, 0, rec ? &records : NULL, 0, 0, NULL, 0, min_r, min_l};
+    if (top_level(&g, &L, &P, min_l)) acc.err = 1;
     else mbea(&g, &L, &R, &P, &Q, &acc);
     ov_free(&L);
     ov_free(&P);
@@ -427,6 +437,7 @@ typedef struct {
     int64_t nroots;
     uint64_t *out;
     uint64_t *out_b;
+    int32_t min_r, min_l;
     int64_t next;
     pthread_mutex_t mu;
     int err;
@@ -441,7 +452,7 @@ static void run_root(root_job *j, int64_t k)
     if (r < 0 || r >= j->g->nU || j->pos[r] < 0) return; /* isolated: never popped */
     int64_t i = j->pos[r];
     ovec R = {0};
-    oacc acc = {0, 0, 0, 0, NULL, 0, 0, NULL, 0};
+    oacc acc = {0, 0, 0, 0, NULL, 0, 0, NULL, 0, j->min_r, j->min_l};
     mbea_iteration(j->g, j->L, &R, r, j->seq + i + 1, j->nseq - i - 1, j->seq, i, NULL, &acc);
     o[0] = acc.count;
     o[1] = acc.hash;
@@ -466,13 +477,14 @@ static void *root_worker(void *arg)
 
 /*
  * Per-root results: out[4k..4k+3] = (count, hash, nodes, bytes) of the top-level
- * iteration whose candidate is roots[k] (zeros for an isolated vertex), and
- * out_b[k] (when out_b is not NULL) its bytes under the second model.
+ * iteration whose candidate is roots[k] (zeros for a vertex that is never
+ * popped), and out_b[k] (when out_b is not NULL) its bytes under the second
+ * model; min_r, min_l: the size filter as in orc_enumerate.
  * Runs on nthreads POSIX threads. Returns 0 or -1.
  */
 int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
                  const int32_t *v_adj, const int32_t *roots, int64_t nroots, uint64_t *out, int32_t nthreads,
-                 uint64_t *out_b)
+                 uint64_t *out_b, int32_t min_r, int32_t min_l)
 {
     ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
     ovec L = {0}, P = {0};
@@ -480,7 +492,7 @@ int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_
     okey *ord = NULL;
     int32_t *seq = NULL;
     int64_t *pos = NULL;
-    if (top_level(&g, &L, &P)) goto done;
+    if (top_level(&g, &L, &P, min_l)) goto done;
     ord = (okey *)malloc((size_t)(P.n ? P.n : 1) * sizeof(okey));
     seq = (int32_t *)malloc((size_t)(P.n ? P.n : 1) * sizeof(int32_t));
     pos = (int64_t *)malloc((size_t)(nU ? nU : 1) * sizeof(int64_t));
@@ -508,6 +520,8 @@ int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_
     job.nroots = nroots;
     job.out = out;
     job.out_b = out_b;
+    job.min_r = min_r;
+    job.min_l = min_l;
     job.next = 0;
     job.err = 0;
     pthread_mutex_init(&job.mu, NULL);
@@ -582,7 +596,7 @@ static void *batch_worker(void *arg)
         const int32_t *uo = j->u_off + j->u_off_start[gi];
         const int32_t *vo = j->v_off + j->v_off_start[gi];
         if (orc_enumerate(j->nU[gi], j->nV[gi], uo, j->u_adj + e0, vo, j->v_adj + e0, j->out + 4 * (int64_t)gi,
-                          NULL, NULL, NULL))
+                          NULL, NULL, NULL, 1, 1))
             j->err = 1;
     }
     return NULL;

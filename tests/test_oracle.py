@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import oracle
+import synth
 from tests import helpers as H
 
 MASK = (1 << 64) - 1
@@ -252,3 +253,42 @@ def test_batch_driver_matches_serial():
     out = oracle.batch(b, nthreads=3)
     for i, g in enumerate(gs):
         assert tuple(int(x) for x in out[i]) == oracle.enumerate_graph(g)
+
+
+# ------------------------------------------------------------ size filter
+
+@pytest.mark.parametrize("min_r,min_l", [(1, 2), (2, 1), (2, 2), (3, 4), (5, 2)])
+def test_size_filter_is_the_filtered_set(min_r, min_l):
+    # the size-filtered enumeration returns exactly the maximal bicliques with
+    # |R| >= min_r and |L| >= min_l (its pruning drops only subtrees and
+    # candidates that cannot reach both sizes), with fewer or equal nodes;
+    # on small graphs also against the brute-force closure enumeration
+    rng = np.random.default_rng(100 * min_r + min_l)
+    graphs = [synth.workload("er200x300"), H.crown(7), H.complete(4, 6)]
+    graphs += [H.random_graph(rng, int(rng.integers(2, 12)), int(rng.integers(2, 30)), p) for p in (0.2, 0.4, 0.6)
+               for _ in range(8)]
+    for g in graphs:
+        c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
+        want = [(R, L) for R, L in rec if len(R) >= min_r and len(L) >= min_l]
+        fc, fh, fn, fb, frec = oracle.enumerate_graph(g, records=True, min_r=min_r, min_l=min_l)
+        assert H.canon(frec) == H.canon(want), g.name
+        assert fc == len(want) and fh == sm_hash(want)
+        assert fn <= n
+        if g.nU <= 12:
+            bc, bh, brec = oracle.bruteforce(g, records=True)
+            assert H.canon([(R, L) for R, L in brec if len(R) >= min_r and len(L) >= min_l]) == H.canon(frec)
+        pr = oracle.per_root(g, min_r=min_r, min_l=min_l)
+        assert (int(pr[:, 0].sum()), int(pr[:, 1].sum(dtype=np.uint64)), int(pr[:, 2].sum()),
+                int(pr[:, 3].sum())) == (fc, fh, fn, fb)
+
+
+def test_size_filter_hand_trace():
+    # path u0-v0-u1-v1-u2 (hand trace 1): with |L| >= 2 only ({u1}, {v0, v1})
+    # passes; u0 and u2 (degree 1) are never popped, u1 is (one node)
+    g = H.graph(3, 2, [(0, 0), (1, 0), (1, 1), (2, 1)])
+    c, h, n, b, rec = oracle.enumerate_graph(g, records=True, min_l=2)
+    assert rec == [((1,), (0, 1))] and (c, n) == (1, 1)
+    # with |R| >= 2 both edges' bicliques pass, the star at u1 does not; all
+    # three roots are popped (three nodes), none has a child
+    c, h, n, b, rec = oracle.enumerate_graph(g, records=True, min_r=2)
+    assert H.canon(rec) == [((0, 1), (0,)), ((1, 2), (1,))] and n == 3
