@@ -202,6 +202,12 @@ typedef struct {
                                  the first superset row), 2 = columns (Q and P as one bitset per vertex
                                  of L: checks are ANDs of the |L'| columns), 0 = auto: columns when some
                                  V vertex has at least 256 neighbours, else rows */
+    int32_t min_r;            /* size filter (0 or 1 = none): only the maximal bicliques with |R| >= min_r */
+    int32_t min_l;            /* and |L| >= min_l are counted, hashed and written. The search skips what
+                                 cannot pass: a call recurses only when |L'| - 1 >= min_l and
+                                 |R'| + |P'| >= min_r, a candidate reaching fewer than min_l vertices of
+                                 L' does not enter P', and a root of degree below min_l is never popped
+                                 (nodes and bytes_alg count what was searched) */
 } mbe_options;
 
 /* Fill *opt with the defaults (all "auto"). */

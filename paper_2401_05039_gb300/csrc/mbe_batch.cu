@@ -286,6 +286,9 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
             blocks[k] = std::min(cl[k].shape.blocks, ws.n_warps / wpb);
             a.n_warps = blocks[k] * wpb;
             a.max_words = kMaxBitsetWords;
+            a.min_r = std::max(1, o.min_r);
+            a.min_l = std::max(1, o.min_l);
+            a.lists = (a.min_r > 1 || a.min_l > 1) ? 1 : 0; // the size filter runs in the extended variant
             a.per_task_owner = d.owner;
             a.per_root_mode = 2;
             a.emit = 0;

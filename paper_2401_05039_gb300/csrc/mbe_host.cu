@@ -294,7 +294,10 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         const int blocks = std::min(shape.blocks, ws.n_warps / wpb);
         a.n_warps = blocks * wpb;
         a.max_words = o.bitset_max_words > 0 ? std::min(o.bitset_max_words, kMaxBitsetWords) : kMaxBitsetWords;
-        a.lists = in.max_deg > 64 * a.max_words ? 1 : 0; // some root needs the sorted-list path
+        a.min_r = std::max(1, o.min_r);
+        a.min_l = std::max(1, o.min_l);
+        // the extended kernel variant: some root needs the sorted-list path, or a size filter is set
+        a.lists = (in.max_deg > 64 * a.max_words || a.min_r > 1 || a.min_l > 1) ? 1 : 0;
         a.totals = ws.ctl->totals;
         a.per_task_owner = in.per_owner;
         a.per_root_mode = in.per_mode;
@@ -714,7 +717,7 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
                    bicliques->capacity_bicliques < 0))
         return set_status(out, MBE_ERR_INVALID_ARG);
     if (o.block_threads < 0 || o.blocks_per_sm < 0 || o.watchdog_ms < 0 || o.arena_bytes < 0 || o.layout < 0 ||
-        o.layout > kLayoutColumns || o.bitset_max_words < 0)
+        o.layout > kLayoutColumns || o.bitset_max_words < 0 || o.min_r < 0 || o.min_l < 0)
         return set_status(out, MBE_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     if (g->nU == 0 || g->n_live == 0) return set_status(out, MBE_OK);

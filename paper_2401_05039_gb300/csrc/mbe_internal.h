@@ -54,7 +54,9 @@ struct SearchArgs {
     int32_t n_warps;
     int32_t max_words;    // bitset limit: level sets of more than 64 * max_words vertices use sorted lists
     int32_t lbuf_cap;     // entries of the scratch list for a wide node's L' (the largest U degree)
-    int32_t lists;        // 1: some root exceeds the bitset limit (launch the variant with the list path)
+    int32_t lists;        // 1: launch the extended variant (some root exceeds the bitset limit, or a size
+                          // filter is set)
+    int32_t min_r, min_l; // size filter: only bicliques with |R| >= min_r and |L| >= min_l (1, 1 = all)
 
     // outputs
     unsigned long long *totals;   // [8]: count, hash, nodes, bytes, donations, steals, -, -

@@ -41,7 +41,9 @@ struct __align__(16) ListHdr {
     int32_t depth;  // depth below the root (progress records)
     int64_t bytes;  // size of the frame
     int64_t parent; // offset of the parent frame from the arena base, -1 at the bottom
-    int64_t pad_[2];
+    int32_t rn;     // |R| (exact when bicliques are written or a minimum |R| is set)
+    int32_t pad32_;
+    int64_t pad_;
 };
 static_assert(sizeof(ListHdr) == 80, "list frame header size");
 
@@ -107,10 +109,10 @@ struct ListOut {
 // Defined by the including kernel: the bitset child of a list node, a frame
 // of the kernel's own layout over L' (ascending ids Lp[0..mp), mp at most
 // the bitset limit) with check set Q' (ids Qg[0..nQd)) then P' (sorted keys
-// Pk[0..pn)), R' = merge of Ra (na) and Rb (nb). Returns the frame or NULL
-// (error set).
+// Pk[0..pn)), R' = merge of Ra (na) and Rb (nb), |R'| = rn. Returns the
+// frame or NULL (error set).
 __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv &e, char *cp, const GView &G,
-                                              int graph, int root, int depth, int64_t parent, const int32_t *Lp,
+                                              int graph, int root, int rn, int64_t parent, const int32_t *Lp,
                                               int mp, const int32_t *Qg, int nQd, const uint64_t *Pk, int pn,
                                               uint64_t Rs, const int32_t *Ra, int na, const int32_t *Rb, int nb);
 
@@ -205,7 +207,7 @@ __device__ uint64_t reverse_scan(int lane, const GView &G, const int32_t *Lw, in
 __device__ void write_list_frame(const SearchArgs &a, const ListEnv &e, char *cp, const int32_t *Lw, int m, const int32_t *Qg,
                                  int nQ, const uint64_t *Pk, int nP, const int32_t *Ra, int na, const int32_t *Rb,
                                  int nb, uint64_t Rsum, int root, int graph, int i0, int i1, int depth,
-                                 int64_t parent, int64_t bytes)
+                                 int64_t parent, int64_t bytes, int rn)
 {
     const int lane = e.lane;
     ListFrame D = list_frame_at(cp, m, nQ, nP);
@@ -230,7 +232,9 @@ __device__ void write_list_frame(const SearchArgs &a, const ListEnv &e, char *cp
         h.depth = depth;
         h.bytes = bytes;
         h.parent = parent;
-        h.pad_[0] = h.pad_[1] = 0;
+        h.rn = rn;
+        h.pad32_ = 0;
+        h.pad_ = 0;
         *D.h = h;
     }
     __syncwarp();
@@ -330,14 +334,17 @@ __device__ __noinline__ ListOut list_root(const SearchArgs &a, const ListEnv e, 
             du = G.u_off[u + 1] - G.u_off[u];
             ck = cnt[k];
         }
-        const bool ql = valid && (du < d || (du == d && u < r));
+        // earlier-ranked candidates were popped before r (those below the size
+        // filter never are)
+        const bool earlier = du < d || (du == d && u < r);
+        const bool ql = valid && earlier && du >= a.min_l;
         if (__ballot_sync(kFull, ql && ck == d)) return out; // r's node is not maximal
-        const bool full = valid && !ql && ck == d;
-        const bool ppart = valid && !ql && ck < d;
+        const bool full = valid && !earlier && ck == d;
+        const bool ppart = valid && !earlier && ck < d && ck >= a.min_l;
         if (full) rsum += key_u(u);
-        if (a.emit) {
+        if (a.emit || a.min_r > 1) {
             const unsigned fb = __ballot_sync(kFull, full);
-            if (full) e.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
+            if (a.emit && full) e.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
             nfull += __popc(fb);
         }
         const unsigned qb = __ballot_sync(kFull, ql);
@@ -353,7 +360,8 @@ __device__ __noinline__ ListOut list_root(const SearchArgs &a, const ListEnv e, 
     }
     rsum = warp_sum64(rsum);
     const uint64_t Rs = key_u(r) + rsum;
-    if (first) {
+    const bool pass = 1 + nfull >= a.min_r; // d >= min_l already
+    if (first && pass) {
         uint64_t ls = 0;
         for (int j = lane; j < d; j += 32) ls += key_v(Ln[j]);
         ls = warp_sum64(ls);
@@ -365,7 +373,7 @@ __device__ __noinline__ ListOut list_root(const SearchArgs &a, const ListEnv e, 
         if (lane == 0) e.rtmp[nfull] = r;
         __syncwarp();
         emit::sort_ids(lane, e.hist, e.rtmp, e.psrc2, nfull + 1, a.key_shift);
-        if (first) {
+        if (first && pass) {
             const int nR = 1 + nfull;
             int64_t rec = 0;
             const int64_t pos = emit::reserve(a, lane, 2 + (int64_t)nR + d, &rec);
@@ -382,7 +390,7 @@ __device__ __noinline__ ListOut list_root(const SearchArgs &a, const ListEnv e, 
             }
         }
     }
-    if (pn == 0) return out;
+    if (pn == 0 || d - 1 < a.min_l || 1 + nfull + pn < a.min_r) return out;
 
     const int nR = a.emit ? 1 + nfull : 0;
     const int64_t sz = list_frame_bytes(d, qn, pn, nR);
@@ -395,7 +403,7 @@ __device__ __noinline__ ListOut list_root(const SearchArgs &a, const ListEnv e, 
     warp_sort_impl(lane, e.hist, e.pkey, e.psrc, e.pkey2, e.psrc2, pn, key_bits);
     const int i0 = (int)(((int64_t)pn * part) / parts), i1 = (int)(((int64_t)pn * (part + 1)) / parts);
     write_list_frame(a, e, e.arena, Ln, d, e.qsrc, qn, e.pkey, pn, e.rtmp, nR, nullptr, 0, Rs, r, graph, i0, i1, 1, -1,
-                     sz);
+                     sz, 1 + nfull);
     out.child = e.arena;
     return out;
 }
@@ -467,11 +475,11 @@ __device__ __noinline__ ListOut list_node(const SearchArgs &a, const ListEnv e, 
         const bool isq = valid && k < nq;
         const bool qpart = isq && ck > 0;
         const bool full = valid && !isq && ck == mp;
-        const bool part = valid && !isq && ck > 0 && ck < mp;
+        const bool part = valid && !isq && ck > 0 && ck < mp && ck >= a.min_l;
         if (full) rsum += key_u(u);
-        if (a.emit) {
+        if (a.emit || a.min_r > 1) {
             const unsigned fb = __ballot_sync(kFull, full);
-            if (full) e.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
+            if (a.emit && full) e.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
             nfull += __popc(fb);
         }
         const unsigned qb = __ballot_sync(kFull, qpart);
@@ -490,8 +498,13 @@ __device__ __noinline__ ListOut list_node(const SearchArgs &a, const ListEnv e, 
     uint64_t ls = 0;
     for (int k = lane; k < mp; k += 32) ls += key_v(Lp[k]);
     ls = warp_sum64(ls);
-    out.cnt += 1;
-    out.hash += splitmix(Rs + ls);
+    // size filter (1, 1 by default: every biclique passes)
+    const int rn = F.h->rn + 1 + nfull;
+    const bool pass = rn >= a.min_r && mp >= a.min_l;
+    if (pass) {
+        out.cnt += 1;
+        out.hash += splitmix(Rs + ls);
+    }
 
     if (a.emit) {
         // B = {x} and the candidates that joined R', ascending
@@ -500,7 +513,7 @@ __device__ __noinline__ ListOut list_node(const SearchArgs &a, const ListEnv e, 
         emit::sort_ids(lane, e.hist, e.rtmp, e.psrc2, nfull + 1, a.key_shift);
         const int nR = F.h->nR + nfull + 1;
         int64_t rec = 0;
-        const int64_t pos = emit::reserve(a, lane, 2 + (int64_t)nR + mp, &rec);
+        const int64_t pos = pass ? emit::reserve(a, lane, 2 + (int64_t)nR + mp, &rec) : -1;
         if (pos >= 0) {
             int32_t *o = a.out_ids + pos;
             if (lane == 0) {
@@ -513,7 +526,8 @@ __device__ __noinline__ ListOut list_node(const SearchArgs &a, const ListEnv e, 
             __syncwarp();
         }
     }
-    if (pn == 0) return out;
+    // the child's level sets are smaller than L' and its R within R' u P'
+    if (pn == 0 || mp - 1 < a.min_l || rn + pn < a.min_r) return out;
 
     // Child: P' in pop order (count, id)
     const int key_bits = a.key_shift + (32 - __clz(mp));
@@ -521,8 +535,8 @@ __device__ __noinline__ ListOut list_node(const SearchArgs &a, const ListEnv e, 
     char *cp = fp + F.h->bytes;
     const int nb = a.emit ? nfull + 1 : 0;
     if (mp <= bitset_limit(a)) {
-        out.child = bits_from_lists(a, e, cp, G, F.h->graph, F.h->root, F.h->depth + 1, fp - e.arena, Lp, mp, e.qsrc,
-                                    qn, e.pkey, pn, Rs, F.R, F.h->nR, e.rtmp, nb);
+        out.child = bits_from_lists(a, e, cp, G, F.h->graph, F.h->root, rn, fp - e.arena, Lp, mp, e.qsrc, qn, e.pkey,
+                                    pn, Rs, F.R, F.h->nR, e.rtmp, nb);
         out.abort = out.child == nullptr;
         return out;
     }
@@ -534,7 +548,7 @@ __device__ __noinline__ ListOut list_node(const SearchArgs &a, const ListEnv e, 
         return out;
     }
     write_list_frame(a, e, cp, Lp, mp, e.qsrc, qn, e.pkey, pn, F.R, F.h->nR, e.rtmp, nb, Rs, F.h->root, F.h->graph, 0,
-                     pn, F.h->depth + 1, fp - e.arena, sz);
+                     pn, F.h->depth + 1, fp - e.arena, sz, rn);
     out.child = cp;
     return out;
 }

@@ -189,6 +189,8 @@ extern "C" int mbe_enumerate_noalloc(int32_t nU, int32_t nV, int64_t nE, const i
     a.n_warps = n_warps;
     a.max_words = kMaxBitsetWords;
     a.lists = max_deg > 64 * kMaxBitsetWords ? 1 : 0;
+    a.min_r = 1;
+    a.min_l = 1;
     a.totals = ctl->totals;
     a.per_task_owner = nullptr;
     a.per_root_mode = 1;

@@ -56,6 +56,9 @@
 namespace mbe {
 namespace {
 
+// The extended variant (MBE_LIST_PATH = 1) also carries the size filter.
+constexpr bool kExt = MBE_LIST_PATH != 0;
+
 constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
 // active-word masks lw[32] u64, active-word indices aw[32] i32
@@ -111,7 +114,8 @@ struct __align__(16) FrameHdr {
     int64_t parent;  // offset of the parent frame from the arena base, -1 at the bottom
     int32_t qpos;    // X positions before P (>= nQ: positions of no Q member are zero in every column)
     int32_t copy_hint; // 1 when the last child built from this frame copied its columns uncompressed
-    int32_t pad_[2];
+    int32_t rn;      // |R| (exact when bicliques are written or a minimum |R| is set)
+    int32_t pad_;
 };
 static_assert(sizeof(FrameHdr) == kFrameHdrBytes, "frame header size");
 
@@ -947,12 +951,12 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
             const int k = (t0 + u) * 32 + lane;
             const bool valid = (t0 + u < ntiles) && k > i && k < nP;
             const bool full = valid && cnt[u] == mp;
-            const bool part = valid && cnt[u] > 0 && cnt[u] < mp;
+            const bool part = valid && cnt[u] > 0 && cnt[u] < mp && (!kExt || cnt[u] >= a.min_l);
             const int g = (full || part) ? F.gid[k] : 0;
             if (full) rsum += key_u(g);
-            if (a.emit) {
+            if (a.emit || (kExt && a.min_r > 1)) {
                 const unsigned fb = __ballot_sync(kFull, full);
-                if (full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = g;
+                if (a.emit && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = g;
                 nfull += __popc(fb);
             }
             const unsigned bal = __ballot_sync(kFull, part);
@@ -969,8 +973,13 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const int xg = F.gid[i];
     const uint64_t Rs = F.h->Rsum + key_u(xg) + rsum;
     const uint64_t lsum = sum_keys_v(c, F.Lid, J, mp);
-    c.cnt += 1;
-    c.hash += splitmix(Rs + lsum);
+    // size filter (1, 1 by default: every biclique passes)
+    const int rn = kExt ? F.h->rn + 1 + nfull : 0;
+    const bool pass = !kExt || (rn >= a.min_r && mp >= a.min_l);
+    if (pass) {
+        c.cnt += 1;
+        c.hash += splitmix(Rs + lsum);
+    }
 
     uint64_t t_build = tnow(a);
     if (a.emit) {
@@ -978,8 +987,10 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         if (lane == 0) S.rtmp[nfull] = xg;
         __syncwarp();
         emit::sort_ids(lane, c.hist, S.rtmp, S.psrc2, nfull + 1, a.key_shift);
-        emit_biclique(a, c, F.R, F.h->nR, S.rtmp, nfull + 1, F.Lid, J, mp);
+        if (pass) emit_biclique(a, c, F.R, F.h->nR, S.rtmp, nfull + 1, F.Lid, J, mp);
     }
+    // the child's level sets are smaller than L' and its R within R' u P'
+    if (kExt && pn > 0 && (mp - 1 < a.min_l || rn + pn < a.min_r)) pn = 0;
     if (pn > 0) prepare_cm(c, Lw, W);
     if (pn == 0) {
         if (lane == 0) tadd(a, c, 2, t_build);
@@ -1081,7 +1092,8 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         h.parent = fp - c.arena;
         h.qpos = qposd;
         h.copy_hint = 1;
-        h.pad_[0] = h.pad_[1] = 0;
+        h.rn = rn;
+        h.pad_ = 0;
         *D.h = h;
         tadd(a, c, 2, t_build);
     }
@@ -1097,7 +1109,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 // Q' u P' adjacent to L'[j]; the rows of P' are copied into the frame, and
 // Q' and P' are transposed into its columns.
 __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv &e, char *cp, const GView &G,
-                                              int graph, int root, int depth, int64_t parent, const int32_t *Lp,
+                                              int graph, int root, int rn, int64_t parent, const int32_t *Lp,
                                               int mp, const int32_t *Qg, int nQd, const uint64_t *Pk, int pn,
                                               uint64_t Rs, const int32_t *Ra, int na, const int32_t *Rb, int nb)
 {
@@ -1153,7 +1165,8 @@ __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv
         h.parent = parent;
         h.qpos = nQd;
         h.copy_hint = 1;
-        h.pad_[0] = h.pad_[1] = 0;
+        h.rn = rn;
+        h.pad_ = 0;
         *D.h = h;
     }
     __syncwarp();
@@ -1205,11 +1218,12 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     const uint64_t t_root = tnow(a);
     const int ro = G.u_off[r];
     const int d = G.u_off[r + 1] - ro;
+    // never popped: an isolated vertex, or one of degree below the size filter
+    if (d == 0 || (kExt && d < a.min_l)) return false;
     // a pre-split root: every part rebuilds the root node, part 0 alone
     // counts it, and part p pops its own contiguous share of P'
     const bool first = part == 0;
     if (first) c.nodes += 1;
-    if (d == 0) return false;
     const int W = (d + 63) >> 6;
     if (W > a.max_words) { // a sorted-list level set
         if constexpr (kLists) {
@@ -1344,18 +1358,21 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
             u = S.ugid[k];
             du = G.u_off[u + 1] - G.u_off[u];
         }
-        bool ql = valid && (du < d || (du == d && u < r));
+        // earlier-ranked candidates were popped before r (those below the size
+        // filter never are); cnt > 0 for every discovered candidate
+        const bool earlier = du < d || (du == d && u < r);
+        bool ql = valid && earlier && (!kExt || du >= a.min_l);
         if (__ballot_sync(kFull, ql && cnt == d)) { // r's node is not maximal
             if (lane == 0) tadd(a, c, 0, t_root);
             return false;
         }
-        bool full = valid && !ql && cnt == d;
-        bool qpart = ql; // cnt > 0 for every discovered candidate
-        bool ppart = valid && !ql && cnt < d;
+        bool full = valid && !earlier && cnt == d;
+        bool qpart = ql;
+        bool ppart = valid && !earlier && cnt < d && (!kExt || cnt >= a.min_l);
         if (full) rsum += key_u(u);
-        if (a.emit) {
+        if (a.emit || (kExt && a.min_r > 1)) {
             unsigned fb = __ballot_sync(kFull, full);
-            if (full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
+            if (a.emit && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
             nfull += __popc(fb);
         }
         unsigned qb = __ballot_sync(kFull, qpart);
@@ -1374,7 +1391,8 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     uint64_t ls = 0;
     for (int j = lane; j < d; j += 32) ls += key_v(Ln[j]);
     ls = warp_sum64(ls);
-    if (first) {
+    const bool pass = !kExt || 1 + nfull >= a.min_r; // d >= min_l already
+    if (first && pass) {
         c.cnt += 1;
         c.hash += splitmix(Rs + ls);
     }
@@ -1385,7 +1403,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         if (lane == 0) S.rtmp[nfull] = r;
         __syncwarp();
         emit::sort_ids(lane, c.hist, S.rtmp, S.psrc2, nfull + 1, a.key_shift);
-        if (first) {
+        if (first && pass) {
             const int nR = 1 + nfull;
             int64_t rec = 0;
             const int64_t pos = emit::reserve(a, lane, 2 + (int64_t)nR + d, &rec);
@@ -1402,7 +1420,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
             }
         }
     }
-    if (pn == 0) {
+    if (pn == 0 || (kExt && (d - 1 < a.min_l || 1 + nfull + pn < a.min_r))) {
         if (lane == 0) tadd(a, c, 0, t_root);
         return false;
     }
@@ -1447,7 +1465,8 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         h.parent = -1;
         h.qpos = qn;
         h.copy_hint = 1;
-        h.pad_[0] = h.pad_[1] = 0;
+        h.rn = 1 + nfull;
+        h.pad_ = 0;
         *D.h = h;
         tadd(a, c, 0, t_root);
     }

@@ -54,8 +54,8 @@ def test_struct_layouts_match_c(tmp_path):
 #include "{HEADER}"
 int main(void) {{
   printf("%zu %zu %zu\\n", sizeof(mbe_options), sizeof(mbe_result), sizeof(mbe_biclique_buffer));
-  printf("%zu %zu %zu %zu\\n", offsetof(mbe_options, arena_bytes), offsetof(mbe_options, model),
-         offsetof(mbe_options, per_root), offsetof(mbe_options, n_exec));
+  printf("%zu %zu %zu %zu %zu\\n", offsetof(mbe_options, arena_bytes), offsetof(mbe_options, model),
+         offsetof(mbe_options, per_root), offsetof(mbe_options, n_exec), offsetof(mbe_options, min_l));
   printf("%zu %zu %zu\\n", offsetof(mbe_result, device_ms), offsetof(mbe_result, status),
          offsetof(mbe_result, n_donations));
   printf("%zu %zu %zu %zu %zu\\n", offsetof(mbe_options, layout), sizeof(mbe_class_params),
@@ -69,10 +69,10 @@ int main(void) {{
     vals = [int(x) for x in out]
     O, R, B = m.Options, m.Result, m.BicliqueBuffer
     assert vals[:3] == [ctypes.sizeof(O), ctypes.sizeof(R), ctypes.sizeof(B)]
-    assert vals[3:7] == [O.arena_bytes.offset, O.model.offset, O.per_root.offset, O.n_exec.offset]
-    assert vals[7:10] == [R.device_ms.offset, R.status.offset, R.n_donations.offset]
+    assert vals[3:8] == [O.arena_bytes.offset, O.model.offset, O.per_root.offset, O.n_exec.offset, O.min_l.offset]
+    assert vals[8:11] == [R.device_ms.offset, R.status.offset, R.n_donations.offset]
     C = m.ClassParams
-    assert vals[10:15] == [O.layout.offset, ctypes.sizeof(C), C.layout.offset, C.tuned_ms.offset, C.default_ms.offset]
+    assert vals[11:16] == [O.layout.offset, ctypes.sizeof(C), C.layout.offset, C.tuned_ms.offset, C.default_ms.offset]
 
 
 def test_compress_helper_matches_bit_gather(tmp_path):

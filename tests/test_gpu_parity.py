@@ -411,3 +411,31 @@ def test_watchdog_expires_cleanly(mbe, layout):
     r2 = G.enumerate(layout=layout)
     assert r2.status == 0 and r2.count == 2 ** 18 - 2
     G.close()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("min_r,min_l", [(1, 2), (2, 1), (3, 4), (2, 2)])
+def test_size_filter_matches_oracle(mbe, layout, min_r, min_l):
+    # (|R| >= min_r, |L| >= min_l)-filtered enumeration: count, hash, nodes and
+    # bytes equal the oracle's filtered run (which is pinned to the plain set
+    # filtered by size), on random graphs, a wide graph (sorted-list path) and
+    # with the bicliques written
+    import torch
+    kw = dict(layout=layout, min_r=min_r, min_l=min_l)
+    for g in _random_cases(3000 + 10 * min_r + min_l, 12) + [wide_graphs()[1]]:
+        assert gpu_tuple(run(mbe, g, **kw)) == oracle.enumerate_graph(g, min_r=min_r, min_l=min_l), (g.nU, g.nV)
+    g = synth.workload("er200x300")
+    c, h, n, b, rec = oracle.enumerate_graph(g, records=True, min_r=min_r, min_l=min_l)
+    G = mbe.Graph.from_synth(g)
+    buf = mbe.Bicliques.allocate(200000, 10000)
+    r = G.enumerate(emit=1, bicliques=buf.buf, **kw)
+    torch.cuda.synchronize()
+    got = raw_records(buf)
+    assert gpu_tuple(r) == (c, h, n, b)
+    assert sorted(got) == sorted(rec) and all(len(R) >= min_r and len(L) >= min_l for R, L in got)
+    # the batch path applies the same filter per graph
+    sub = [H.random_graph(np.random.default_rng(k), 40, 90, 0.2) for k in range(6)]
+    per, tot = mbe.enumerate_batch(synth.pack(sub), **kw)
+    for x, p in zip(sub, per):
+        assert gpu_tuple(p) == oracle.enumerate_graph(x, min_r=min_r, min_l=min_l)
+    G.close()
