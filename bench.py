@@ -304,6 +304,12 @@ def measure_learned(m, torch):
                 best = (t, r)
         return best
 
+    def ideal_order(g, pr):
+        # the order a perfect cost predictor would give: roots by measured subtree nodes, descending
+        live = np.nonzero(np.diff(g.u_off) > 0)[0]
+        o = live[np.argsort(-pr[live, 2].astype(np.int64), kind="stable")].astype(np.int32)
+        return torch.from_numpy(o).cuda(), int(o.shape[0])
+
     g = synth.workload("chunglu200k")
     G = m.Graph.from_synth(g)
     G.enumerate(schedule=1, model=model)  # warm-up: sizes the workspace, caches the features
@@ -311,7 +317,10 @@ def measure_learned(m, torch):
     ts, rs = timed(G)
     tl, rl = timed(G, schedule=1, model=model)
     to, ro = timed(G, schedule=2, model=model)
+    io, n_io = ideal_order(g, pr)
+    ti, ri = timed(G, exec_order=io, n_exec=n_io)
     assert (rl.count, rl.hash, rl.nodes) == (rs.count, rs.hash, rs.nodes) == (ro.count, ro.hash, ro.nodes)
+    assert (ri.count, ri.hash, ri.nodes) == (rs.count, rs.hash, rs.nodes)
     pred = model.predict(G.features()).cpu().numpy()
     live = np.nonzero(np.diff(g.u_off) > 0)[0]
     from scipy.stats import spearmanr
@@ -325,6 +334,10 @@ def measure_learned(m, torch):
     s20, r20 = timed(G)
     o20, q20 = timed(G, schedule=2, model=model)
     l20, p20 = timed(G, schedule=1, model=model)
+    _, pr20 = G.per_root()
+    io20, n_io20 = ideal_order(g20, pr20)
+    i20, ri20 = timed(G, exec_order=io20, n_exec=n_io20)
+    assert (ri20.count, ri20.hash, ri20.nodes) == (r20.count, r20.hash, r20.nodes)
     sn, rn = timed(G, reps=1, steal=0)
     ln, qn = timed(G, reps=1, steal=0, schedule=1, model=model)
     assert len({(x.count, x.hash, x.nodes) for x in (r20, q20, p20, rn, qn)}) == 1
@@ -332,13 +345,13 @@ def measure_learned(m, torch):
     model.close()
     best_200k = min(tl, to)
     return {"workload": "chunglu200k (200,000 x 1,000,000, 5,000,000 edges, exponents 2.0/2.2, cap 400, seed 4)",
-            "count": int(rs.count), "static_ms": ts, "learned_ms": tl,
+            "count": int(rs.count), "static_ms": ts, "learned_ms": tl, "ideal_order_ms": ti,
             "learned_search_ms": rl.device_ms, "learned_prep_ms": rl.prep_ms,
             "learned_order_only_ms": to,
             "static_bicliques_per_s": rs.count / (ts * 1e-3),
             "learned_bicliques_per_s": rs.count / (best_200k * 1e-3),
             "speedup_learned_over_static": ts / best_200k,
-            "chunglu20k": {"static_ms": s20, "learned_order_only_ms": o20, "learned_ms": l20,
+            "chunglu20k": {"static_ms": s20, "learned_order_only_ms": o20, "learned_ms": l20, "ideal_order_ms": i20,
                            "speedup_learned_order_over_static": s20 / o20,
                            "no_stealing": {"static_ms": sn, "learned_split_ms": ln, "speedup": sn / ln}},
             "model": {"train_graphs": "2 Chung-Lu 20k-shaped (seeds 100, 101) + 2 planted 5k-shaped (seeds 200, 201)",

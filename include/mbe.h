@@ -229,8 +229,11 @@ typedef struct {
 } mbe_result;
 
 /*
- * Caller-owned DEVICE buffers for the bicliques themselves (emit = 1; the
- * emit step of Algorithm 1). Biclique b is the record at ids[offsets[b]]:
+ * Caller-owned buffers for the bicliques themselves (emit = 1; the emit
+ * step of Algorithm 1), in device memory or in pinned host memory that the
+ * device can address (cudaHostAlloc / cudaHostRegister): the kernels write
+ * the records directly, so an output larger than device memory can go
+ * straight to the host. Biclique b is the record at ids[offsets[b]]:
  * |R|, |L|, then R's ids in ascending order, then L's ids in ascending
  * order (ids of the caller's U and V). Records appear in any order.
  *

@@ -75,6 +75,8 @@ constexpr int kCompressNum = 1, kCompressDen = 4;
 // roots whose neighbours' degrees sum to at least this order L by degree class
 constexpr int64_t kDegSortMin = 8192;
 
+
+
 __device__ __forceinline__ unsigned lanemask_lt()
 {
     unsigned m;
@@ -694,15 +696,13 @@ __device__ int q_union_copy(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t 
 
 // Compression of the prefix by mq: offq = per-word exclusive popcount
 // prefix, cmq = compress stage masks of every word.
-__device__ void q_compress_masks(Ctx &c, int LW)
+__device__ void q_compress_masks(int lane, const uint64_t *mq, int32_t *offq, uint64_t *cmq, int LW)
 {
-    const int lane = c.lane;
-    Scratch &S = c.s;
     int run = 0;
     for (int w0 = 0; w0 < LW; w0 += 32) {
         const int w = w0 + lane;
         const bool v = w < LW;
-        const uint64_t m = v ? S.mq[w] : 0ULL;
+        const uint64_t m = v ? mq[w] : 0ULL;
         const int pc = __popcll(m);
         int incl = pc;
 #pragma unroll
@@ -711,10 +711,10 @@ __device__ void q_compress_masks(Ctx &c, int LW)
             if (lane >= o) incl += y;
         }
         if (v) {
-            S.offq[w] = run + incl - pc;
+            offq[w] = run + incl - pc;
             CompressMasks cm = compress_prepare_rolled(m);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) S.cmq[6 * (int64_t)w + i] = cm.mv[i];
+            for (int i = 0; i < 6; ++i) cmq[6 * (int64_t)w + i] = cm.mv[i];
         }
         run += __shfl_sync(kFull, incl, 31);
     }
@@ -725,10 +725,9 @@ __device__ void q_compress_masks(Ctx &c, int LW)
 // last word cut by `last`, copied without compression: positions outside Q'
 // are zero in every column of L' already. Words [LW, QWd) are zeroed for
 // the P' bits that follow.
-__device__ void q_copy_columns(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
+__device__ void q_copy_columns(int lane, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
                                uint64_t *dst, int QWd)
 {
-    const int lane = c.lane;
     // mp * QWd words: the frame fits the stack, far below 2^31 words
     const unsigned total = (unsigned)mp * (unsigned)QWd;
     for (unsigned b = 0; b < total; b += 32 * kCopyLoads) {
@@ -761,11 +760,9 @@ __device__ void q_copy_columns(Ctx &c, const uint64_t *Q, int QW, int LW, uint64
 // column is compressed lane-wise and assembled in shared memory, then
 // written out; only the first word of a chunk can hold bits of the previous
 // chunk (it is OR-ed). dst is zeroed.
-__device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, int LW, const int32_t *J, int mp, uint64_t *dst,
-                                int QWd)
+__device__ void q_child_columns(int lane, const uint64_t *mq, const uint64_t *cmq, const int32_t *offq, uint64_t *sbuf,
+                                const uint64_t *Q, int QW, int LW, const int32_t *J, int mp, uint64_t *dst, int QWd)
 {
-    const int lane = c.lane;
-    Scratch &S = c.s;
     if (LW <= 8) {
         // short columns: one lane per child column, bits appended in registers
         for (int t = lane; t < mp; t += 32) {
@@ -775,9 +772,9 @@ __device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, int LW, const
             int o = 0, b = 0;
             for (int w = 0; w < LW; ++w) {
                 CompressMasks cm;
-                cm.m = S.mq[w];
+                cm.m = mq[w];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) cm.mv[i] = S.cmq[6 * (int64_t)w + i];
+                for (int i = 0; i < 6; ++i) cm.mv[i] = cmq[6 * (int64_t)w + i];
                 const int nb = __popcll(cm.m);
                 if (nb == 0) continue;
                 const uint64_t v = compress_apply(col[w], cm);
@@ -805,12 +802,12 @@ __device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, int LW, const
             int nb = 0, off = 0;
             if (v) {
                 CompressMasks cm;
-                cm.m = S.mq[w];
+                cm.m = mq[w];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) cm.mv[i] = S.cmq[6 * (int64_t)w + i];
+                for (int i = 0; i < 6; ++i) cm.mv[i] = cmq[6 * (int64_t)w + i];
                 val = compress_apply(col[w], cm);
                 nb = __popcll(cm.m);
-                off = S.offq[w];
+                off = offq[w];
             }
             const int first = __shfl_sync(kFull, off, 0);
             const int k0 = first >> 6;
@@ -818,18 +815,18 @@ __device__ void q_child_columns(Ctx &c, const uint64_t *Q, int QW, int LW, const
             const int end_bit = __shfl_sync(kFull, off + nb, last_lane);
             if (end_bit == first) continue;
             const int k1 = (end_bit - 1) >> 6;
-            for (int q = lane; q <= k1 - k0; q += 32) c.sbuf[q] = 0;
+            for (int q = lane; q <= k1 - k0; q += 32) sbuf[q] = 0;
             __syncwarp();
             if (nb) {
                 const int rel = off - (k0 << 6);
                 const int kk = rel >> 6, b = rel & 63;
-                atomicOr(reinterpret_cast<unsigned long long *>(&c.sbuf[kk]), (unsigned long long)(val << b));
+                atomicOr(reinterpret_cast<unsigned long long *>(&sbuf[kk]), (unsigned long long)(val << b));
                 if (b + nb > 64)
-                    atomicOr(reinterpret_cast<unsigned long long *>(&c.sbuf[kk + 1]),
+                    atomicOr(reinterpret_cast<unsigned long long *>(&sbuf[kk + 1]),
                              (unsigned long long)(val >> (64 - b)));
             }
             __syncwarp();
-            for (int q = lane; q <= k1 - k0; q += 32) out[k0 + q] = q == 0 ? (out[k0] | c.sbuf[0]) : c.sbuf[q];
+            for (int q = lane; q <= k1 - k0; q += 32) out[k0 + q] = q == 0 ? (out[k0] | sbuf[0]) : sbuf[q];
             __syncwarp();
         }
     }
@@ -1023,7 +1020,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         nQd = q_union(c, F.Q, QW, LW, last, J, mp);
     const bool compress = kCompressDen * ((nQd + 63) >> 6) <= kCompressNum * LW;
     if (lane == 0) F.h->copy_hint = compress ? 0 : 1;
-    if (compress && nQd > 0) q_compress_masks(c, LW);
+    if (compress && nQd > 0) q_compress_masks(lane, S.mq, S.offq, S.cmq, LW);
     if (lane == 0) {
         tadd(a, c, 15, t_qc);
         tadd(a, c, 16, t_qc);
@@ -1061,9 +1058,9 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     t_qc = tnow(a);
     if (compress) {
         zero_words(c, D.Q, (int64_t)mp * QWd);
-        if (nQd > 0) q_child_columns(c, F.Q, QW, LW, J, mp, D.Q, QWd);
+        if (nQd > 0) q_child_columns(lane, S.mq, S.cmq, S.offq, c.sbuf, F.Q, QW, LW, J, mp, D.Q, QWd);
     } else if (!spec) {
-        q_copy_columns(c, F.Q, QW, LW, last, J, mp, D.Q, QWd);
+        q_copy_columns(lane, F.Q, QW, LW, last, J, mp, D.Q, QWd);
     }
     const uint64_t t_tr = tnow(a);
     rows_to_columns(lane, D.rows, Wd, nullptr, pn, mp, D.Q, QWd, qposd);

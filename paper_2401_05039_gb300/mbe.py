@@ -199,6 +199,37 @@ class Graph:
             _check(st, "mbe_enumerate")
         return r
 
+    def iter_bicliques(self, capacity_ids=1 << 24, capacity_bicliques=1 << 20, pinned_host=True, stream=None,
+                       **kw):
+        """Every maximal biclique as (R, L) id tuples (each ascending), in bounded memory.
+
+        The roots of the static order are taken in contiguous shards
+        (root_begin / root_end); each shard is enumerated into one reused
+        buffer of the given capacities, in pinned host memory by default (the
+        kernels write it directly), and a shard whose output does not fit is
+        halved and run again. kw are further mbe_options fields (layout,
+        min_r, min_l, ...). The shards' bicliques are those of the whole graph.
+        """
+        import torch
+        u_off = self._keep[0]
+        deg = u_off[1:] - u_off[:-1]
+        n_roots = int((deg > 0).sum())
+        buf = Bicliques.allocate(capacity_ids, capacity_bicliques, pinned_host=pinned_host)
+        stack = [(0, n_roots)]
+        while stack:
+            b, e = stack.pop()
+            if b >= e:
+                continue
+            r = self.enumerate(stream=stream, bicliques=buf.buf, check=False, emit=1, root_begin=b, root_end=e, **kw)
+            if r.status == 5 and e - b > 1:  # MBE_ERR_OUTPUT_FULL: split the shard
+                mid = (b + e) // 2
+                stack.append((mid, e))
+                stack.append((b, mid))
+                continue
+            _check(r.status, "mbe_enumerate")
+            torch.cuda.synchronize()
+            yield from buf.records()
+
     def features(self, stream=None, raw=False):
         """mbe_root_features: float32 [nU, 8] CUDA tensor (and the raw int32 values with raw=True)."""
         import torch
@@ -387,12 +418,25 @@ class Bicliques:
     buf: BicliqueBuffer
 
     @classmethod
-    def allocate(cls, capacity_ids: int, capacity_bicliques: int):
+    def allocate(cls, capacity_ids: int, capacity_bicliques: int, pinned_host: bool = False):
+        """Buffers in device memory, or (pinned_host) in pinned host memory that the kernels write directly."""
         import torch
-        ids = torch.empty(max(capacity_ids, 1), dtype=torch.int32, device="cuda")
-        offs = torch.empty(max(capacity_bicliques, 1), dtype=torch.int64, device="cuda")
+        if pinned_host:
+            ids = torch.empty(max(capacity_ids, 1), dtype=torch.int32).pin_memory()
+            offs = torch.empty(max(capacity_bicliques, 1), dtype=torch.int64).pin_memory()
+        else:
+            ids = torch.empty(max(capacity_ids, 1), dtype=torch.int32, device="cuda")
+            offs = torch.empty(max(capacity_bicliques, 1), dtype=torch.int64, device="cuda")
         buf = BicliqueBuffer(ids.data_ptr(), capacity_ids, offs.data_ptr(), capacity_bicliques, 0, 0)
         return cls(ids, offs, buf)
+
+    def records(self):
+        """The (R, L) id tuples as written (each side already ascending)."""
+        n = int(self.buf.n_bicliques_written)
+        ids = self.ids.cpu().numpy()
+        for o in self.offsets[:n].cpu().numpy().tolist():
+            nr, nl = int(ids[o]), int(ids[o + 1])
+            yield tuple(ids[o + 2:o + 2 + nr].tolist()), tuple(ids[o + 2 + nr:o + 2 + nr + nl].tolist())
 
     def decode(self):
         """List of (R, L) sorted tuples for the bicliques written."""

@@ -439,3 +439,24 @@ def test_size_filter_matches_oracle(mbe, layout, min_r, min_l):
     for x, p in zip(sub, per):
         assert gpu_tuple(p) == oracle.enumerate_graph(x, min_r=min_r, min_l=min_l)
     G.close()
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_bicliques_to_pinned_host_memory_in_shards(mbe, layout):
+    # the kernels write the records straight into pinned host buffers; with a
+    # buffer far smaller than the output, the shard iterator splits the root
+    # order until every shard fits, and the shards' records are exactly the
+    # oracle's set (size filter included)
+    import torch
+    g = synth.workload("er200x300")
+    _, _, _, _, rec = oracle.enumerate_graph(g, records=True)
+    G = mbe.Graph.from_synth(g)
+    buf = mbe.Bicliques.allocate(200000, 10000, pinned_host=True)
+    r = G.enumerate(emit=1, bicliques=buf.buf, layout=layout)
+    torch.cuda.synchronize()
+    assert r.count == len(rec) and sorted(buf.records()) == sorted(rec)
+    got = list(G.iter_bicliques(capacity_ids=4000, capacity_bicliques=400, layout=layout))
+    assert sorted(got) == sorted(rec)
+    got = list(G.iter_bicliques(capacity_ids=4000, capacity_bicliques=400, layout=layout, min_r=2, min_l=3))
+    assert sorted(got) == sorted(oracle.enumerate_graph(g, records=True, min_r=2, min_l=3)[4])
+    G.close()
