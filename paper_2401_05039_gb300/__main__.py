@@ -16,7 +16,8 @@ import sys
 
 def main() -> int:
     ap = argparse.ArgumentParser(prog="python -m paper_2401_05039_gb300")
-    ap.add_argument("workload", help="er200x300 | chunglu20k | planted5k | chunglu200k")
+    ap.add_argument("workload", help="er200x300 | chunglu20k | planted5k | chunglu200k | batchgraph:<i> (graph i "
+                                     "of the 4,096-graph batch)")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--schedule", type=int, default=0)
     ap.add_argument("--steal", type=int, default=1)
@@ -32,7 +33,10 @@ def main() -> int:
     from . import mbe
 
     mbe.load()
-    g = synth.workload(args.workload)
+    if args.workload.startswith("batchgraph:"):
+        g = synth.batch_graph(3 + int(args.workload.split(":", 1)[1]))
+    else:
+        g = synth.workload(args.workload)
     G = mbe.Graph.from_synth(g)
     free0 = torch.cuda.mem_get_info()[0]
     for k in range(args.repeat):

@@ -1695,7 +1695,7 @@ __device__ void finish_task(const SearchArgs &a, Ctx &c, int owner)
 #ifndef MBE_SEARCH_MIN_BLOCKS
 #define MBE_SEARCH_MIN_BLOCKS 2 // resident 256-thread blocks per SM the register budget is sized for
 #endif
-__global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) MBE_SEARCH_KERNEL(SearchArgs a)
+__global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) MBE_SEARCH_KERNEL(const __grid_constant__ SearchArgs a)
 {
     extern __shared__ uint32_t smem[];
     Ctx c;

@@ -295,14 +295,20 @@ def test_chunglu20k_roots(mbe, golden_dir, layout):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS)
-def test_chunglu200k_sampled_roots(mbe, golden_dir, layout):
+def test_chunglu200k_whole_graph(mbe, golden_dir, layout):
+    # the 200k x 1M Chung-Lu workload: the whole-graph oracle total (count,
+    # hash, nodes, bytes), its stored per-root rows (a seeded random sample,
+    # the 100 heaviest roots and a sample of high-degree roots), and per-root
+    # rows adding up to the total
     gold = _golden(golden_dir, "chunglu200k")
     g = synth.workload("chunglu200k")
     assert g.digest() == gold["graph"]["digest"]
     r, got = _check_per_root_rows(mbe, g, gold, layout=layout)
-    # whole-graph consistency: per-root rows add up to the totals
     assert int(got[:, 0].sum()) == r.count
     assert int(got[:, 2].sum()) == r.nodes
+    t = gold["total"]
+    assert t is not None
+    assert gpu_tuple(r) == (t["count"], int(t["hash"], 16), t["nodes"], t["bytes"])
 
 
 def test_invalid_layout_rejected(mbe):
