@@ -49,10 +49,11 @@ def _load():
             lib.orc_sm.argtypes = [ctypes.c_uint64]
             lib.orc_sm.restype = ctypes.c_uint64
             lib.orc_enumerate.argtypes = [ctypes.c_int32, ctypes.c_int32, _I32P, _I32P, _I32P, _I32P, _U64P,
-                                          ctypes.POINTER(_I32P), _I64P, _U64P, ctypes.c_int32, ctypes.c_int32]
+                                          ctypes.POINTER(_I32P), _I64P, _U64P, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32]
             lib.orc_per_root.argtypes = [ctypes.c_int32, ctypes.c_int32, _I32P, _I32P, _I32P, _I32P, _I32P,
                                          ctypes.c_int64, _U64P, ctypes.c_int32, _U64P, ctypes.c_int32,
-                                         ctypes.c_int32]
+                                         ctypes.c_int32, ctypes.c_int32]
             lib.orc_root_order.argtypes = [ctypes.c_int32, _I32P, _I32P, _I64P]
             lib.orc_batch.argtypes = [ctypes.c_int32, _I32P, _I32P, _I64P, _I64P, _I64P, _I32P, _I32P, _I32P,
                                       _I32P, _I32P, _U64P, ctypes.c_int32]
@@ -100,7 +101,8 @@ def _arrays(g):
     return _c32(g.u_off), _c32(g.u_adj), _c32(g.v_off), _c32(g.v_adj)
 
 
-def enumerate_graph(g, records: bool = False, bytes_b: bool = False, min_r: int = 1, min_l: int = 1):
+def enumerate_graph(g, records: bool = False, bytes_b: bool = False, min_r: int = 1, min_l: int = 1,
+                    prune: bool = False):
     """Serial MBEA over the whole graph.
 
     Returns ``(count, hash, nodes, bytes)`` or, with ``records=True``,
@@ -109,7 +111,9 @@ def enumerate_graph(g, records: bool = False, bytes_b: bool = False, min_r: int 
     appends the count under the second byte model (bitset rows or reverse-
     scanned lists, whichever is cheaper per node). ``min_r``, ``min_l``: the
     size filter (only bicliques with |R| >= min_r and |L| >= min_l, and no
-    search where none can pass).
+    search where none can pass). ``prune=True``: iMBE's L - L' removal
+    (Section II-C): the same bicliques from fewer nodes; the second byte
+    model is then not counted (0).
     """
     lib = _load()
     uo, ua, vo, va = _arrays(g)
@@ -118,7 +122,7 @@ def enumerate_graph(g, records: bool = False, bytes_b: bool = False, min_r: int 
     rec_p, rec_n = _I32P(), ctypes.c_int64(0)
     rc = lib.orc_enumerate(g.nU, g.nV, _p32(uo), _p32(ua), _p32(vo), _p32(va), out.ctypes.data_as(_U64P),
                            ctypes.byref(rec_p) if records else None, ctypes.byref(rec_n) if records else None,
-                           ob.ctypes.data_as(_U64P), int(min_r), int(min_l))
+                           ob.ctypes.data_as(_U64P), int(min_r), int(min_l), int(bool(prune)))
     if rc:
         raise MemoryError("oracle enumeration failed")
     res = tuple(int(x) for x in out)
@@ -129,12 +133,14 @@ def enumerate_graph(g, records: bool = False, bytes_b: bool = False, min_r: int 
     return res
 
 
-def per_root(g, roots=None, nthreads: int = 1, bytes_b: bool = False, min_r: int = 1, min_l: int = 1):
+def per_root(g, roots=None, nthreads: int = 1, bytes_b: bool = False, min_r: int = 1, min_l: int = 1,
+             prune: bool = False):
     """(count, hash, nodes, bytes) per top-level candidate; uint64 array [len(roots), 4].
 
     ``roots`` defaults to every U vertex (row u = vertex u). With
     ``bytes_b=True`` the rows have a fifth column: bytes under the second
-    byte model.
+    byte model. ``prune``: as in :func:`enumerate_graph` (a root that the
+    pruning removes gets a zero row).
     """
     lib = _load()
     uo, ua, vo, va = _arrays(g)
@@ -144,7 +150,8 @@ def per_root(g, roots=None, nthreads: int = 1, bytes_b: bool = False, min_r: int
     if roots.shape[0] == 0:
         return np.zeros((0, 5), dtype=np.uint64) if bytes_b else out
     rc = lib.orc_per_root(g.nU, g.nV, _p32(uo), _p32(ua), _p32(vo), _p32(va), _p32(roots), roots.shape[0],
-                          out.ctypes.data_as(_U64P), nthreads, ob.ctypes.data_as(_U64P), int(min_r), int(min_l))
+                          out.ctypes.data_as(_U64P), nthreads, ob.ctypes.data_as(_U64P), int(min_r), int(min_l),
+                          int(bool(prune)))
     if rc:
         raise MemoryError("oracle per-root run failed")
     if bytes_b:

@@ -27,7 +27,8 @@
  *    loop of one call, so these keys do not change while the loop runs and
  *    the sequence of pops is P sorted by (|N(v) n L|, id); the oracle sorts
  *    once per call instead of rescanning P before every pop.
- *  - A vertex of P that joins R' stays in P (no L - L' removal, no pivots).
+ *  - A vertex of P that joins R' stays in P (no L - L' removal, no pivots),
+ *    unless the pruned mode is asked for (see twin_reps below).
  *  - "nodes" counts the iterations of the while loop (every candidate that
  *    was popped, including those whose node fails the maximality check).
  *
@@ -155,6 +156,7 @@ typedef struct {
     const int32_t *rootL;  /* L of the current root's level-1 call, N(r), sorted */
     int64_t nRootL;
     int32_t min_r, min_l;  /* size filter: only bicliques with |R| >= min_r and |L| >= min_l (1, 1 = all) */
+    int32_t prune;         /* iMBE's L - L' removal (Section II-C), see twin_reps */
 } oacc;
 
 /*
@@ -218,6 +220,85 @@ static void emit(oacc *acc, const ovec *L, const ovec *R)
         free(rs);
         if (bad) acc->err = 1;
     }
+}
+
+/* ------------------------------------------------- pruned mode (iMBE) */
+/*
+ * Embedded pruning by L - L' removal (paper Section II-C, after Zhang et al.'s
+ * iMBEA): while x's node expands, a candidate v of P that is adjacent to all
+ * of L' and to nothing in L - L' leaves P. Such a v has N(v) n L = L' =
+ * N(x) n L: it is a twin of x within L. Every biclique that a later sibling
+ * could reach through v has its L inside N(v) n L = N(x) n L, so it also
+ * fits x, which is in Q by then: the node is rejected anyway, and so is any
+ * node that v would start at its own turn. Removing v therefore changes no
+ * output, only the number of nodes. (Nor is v needed in Q: for every later
+ * sibling and every node below it, x's test against Q gives the same answer
+ * as v's.)
+ *
+ * Reading used here: the removal is applied whether or not x's own node is
+ * maximal. If x's node fails the check, a twin of x fails the same check at
+ * its turn and, in later siblings, can only lead to bicliques whose L is
+ * covered by the Q vertex that rejected x; so the removal is just as safe,
+ * and the removed set becomes a property of the call alone: with the pop
+ * sequence seq[0..nP) fixed at the call's entry, seq[j] is removed from P
+ * for every pop after rep[j], where rep[j] is the first position whose
+ * vertex has the same neighbourhood in L (rep[j] = j when there is none).
+ * At its own turn a removed vertex is skipped: no node, and it does not
+ * join Q.
+ *
+ * twin_reps fills rep[0..nP): it sorts the positions by (|N(v) n L|, the
+ * sorted list N(v) n L, position) and gives every run of equal lists the
+ * position that starts it.
+ */
+typedef struct {
+    const int32_t *a;
+    int64_t n, pos;
+} olist;
+
+static int cmp_olist(const void *x, const void *y)
+{
+    const olist *p = (const olist *)x, *q = (const olist *)y;
+    if (p->n != q->n) return (p->n > q->n) - (p->n < q->n);
+    for (int64_t k = 0; k < p->n; ++k)
+        if (p->a[k] != q->a[k]) return (p->a[k] > q->a[k]) - (p->a[k] < q->a[k]);
+    return (p->pos > q->pos) - (p->pos < q->pos);
+}
+
+static int twin_reps(const ograph *g, const ovec *L, const int32_t *seq, int64_t nP, int64_t *rep)
+{
+    ovec all = {0};
+    int64_t *start = (int64_t *)malloc((size_t)(nP + 1) * sizeof(int64_t));
+    olist *lists = (olist *)malloc((size_t)(nP ? nP : 1) * sizeof(olist));
+    int rc = -1;
+    if (!start || !lists) goto done;
+    for (int64_t i = 0; i < nP; ++i) {
+        int64_t dv;
+        const int32_t *Nv = nbr(g, seq[i], &dv);
+        start[i] = all.n;
+        if (intersect(Nv, dv, L->a, L->n, &all)) goto done;
+    }
+    start[nP] = all.n;
+    for (int64_t i = 0; i < nP; ++i) {
+        lists[i].a = all.a + start[i];
+        lists[i].n = start[i + 1] - start[i];
+        lists[i].pos = i;
+    }
+    qsort(lists, (size_t)nP, sizeof(olist), cmp_olist);
+    for (int64_t k = 0, first = 0; k < nP; ++k) {
+        if (k > 0) {
+            const olist *p = &lists[k - 1], *q = &lists[k];
+            int same = p->n == q->n;
+            for (int64_t t = 0; same && t < p->n; ++t) same = p->a[t] == q->a[t];
+            if (!same) first = k;
+        }
+        rep[lists[k].pos] = lists[first].pos;
+    }
+    rc = 0;
+done:
+    ov_free(&all);
+    free(start);
+    free(lists);
+    return rc;
 }
 
 /* ------------------------------------------------------------ Algorithm 1 */
@@ -292,12 +373,14 @@ static void mbea_iteration(const ograph *g, const ovec *L, const ovec *R, int32_
         acc->bytes += bytes_node(L->n, Lp.n, nQ, n_rest, is_maximal);
         /* sum of cx over L' = L n N(x): both sorted, walk them together */
         uint64_t cx_sum = 0;
-        for (int64_t i = 0, j = 0; i < L->n && j < Lp.n; ++i)
+        for (int64_t i = 0, j = 0; cx && i < L->n && j < Lp.n; ++i)
             if (L->a[i] == Lp.a[j]) {
                 cx_sum += (uint64_t)cx[i];
                 ++j;
             }
-        acc->bytes_b += bytes_node_b(L->n, Lp.n, nQ, n_rest, count_common(Nx, dx, acc->rootL, acc->nRootL), cx_sum);
+        if (cx)
+            acc->bytes_b +=
+                bytes_node_b(L->n, Lp.n, nQ, n_rest, count_common(Nx, dx, acc->rootL, acc->nRootL), cx_sum);
     }
     goto done;
 oom:
@@ -327,11 +410,11 @@ static void mbea(const ograph *g, const ovec *L, const ovec *R, const ovec *P, c
     int64_t nP = P->n;
     okey *ord = (okey *)malloc((size_t)(nP ? nP : 1) * sizeof(okey));
     int32_t *seq = (int32_t *)malloc((size_t)(nP ? nP : 1) * sizeof(int32_t));
-    int32_t *xs = NULL;
-    int64_t *cx = NULL;
+    int32_t *xs = NULL, *rest = NULL;
+    int64_t *cx = NULL, *rep = NULL;
     ovec Qc = {0};
     if (!ord || !seq) goto oom;
-    if (R->n > 0) {
+    if (R->n > 0 && !acc->prune) {
         /* second byte model: cx[k] = |N(L[k]) n X| with X = Q u P, sorted copy */
         xs = (int32_t *)malloc((size_t)(Q->n + nP ? Q->n + nP : 1) * sizeof(int32_t));
         cx = (int64_t *)malloc((size_t)(L->n ? L->n : 1) * sizeof(int64_t));
@@ -356,9 +439,23 @@ static void mbea(const ograph *g, const ovec *L, const ovec *R, const ovec *P, c
     for (int64_t i = 0; i < Q->n; ++i)
         if (ov_push(&Qc, Q->a[i])) goto oom;
 
+    if (acc->prune) {
+        rep = (int64_t *)malloc((size_t)(nP ? nP : 1) * sizeof(int64_t));
+        rest = (int32_t *)malloc((size_t)(nP ? nP : 1) * sizeof(int32_t));
+        if (!rep || !rest || twin_reps(g, L, seq, nP, rep)) goto oom;
+    }
+
     for (int64_t i = 0; i < nP && !acc->err; ++i) { /* while |P| > 0 */
         int32_t x = seq[i];                         /* x = P.pop() */
-        mbea_iteration(g, L, R, x, seq + i + 1, nP - i - 1, Qc.a, Qc.n, cx, acc);
+        if (!rep) {
+            mbea_iteration(g, L, R, x, seq + i + 1, nP - i - 1, Qc.a, Qc.n, cx, acc);
+        } else {
+            if (rep[i] < i) continue; /* left P when its twin seq[rep[i]] was popped */
+            int64_t nr = 0;
+            for (int64_t j = i + 1; j < nP; ++j)
+                if (rep[j] >= i) rest[nr++] = seq[j];
+            mbea_iteration(g, L, R, x, rest, nr, Qc.a, Qc.n, NULL, acc);
+        }
         if (ov_push(&Qc, x)) goto oom; /* Q = Q u {x} */
     }
     goto done;
@@ -369,6 +466,8 @@ done:
     free(seq);
     free(xs);
     free(cx);
+    free(rep);
+    free(rest);
     ov_free(&Qc);
 }
 
@@ -387,18 +486,19 @@ static int top_level(const ograph *g, ovec *L, ovec *P, int32_t min_l)
 
 /*
  * Whole-graph enumeration, serial. out[0..3] = count, hash, nodes, bytes;
- * *out_b (when not NULL) = bytes under the second model. min_r, min_l: the
- * size filter (1, 1 = every maximal biclique). When rec != NULL, *rec receives a malloc'd int32 array of records
+ * *out_b (when not NULL) = bytes under the second model (plain mode only:
+ * 0 when pruning). min_r, min_l: the size filter (1, 1 = every maximal
+ * biclique). prune != 0: iMBE's L - L' removal (see twin_reps). When rec != NULL, *rec receives a malloc'd int32 array of records
  * (|R|, |L|, R..., L...) and *rec_len its length (free with orc_free).
  * Returns 0, or -1 on allocation failure.
  */
 int orc_enumerate(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
                   const int32_t *v_adj, uint64_t *out, int32_t **rec, int64_t *rec_len, uint64_t *out_b,
-                  int32_t min_r, int32_t min_l)
+                  int32_t min_r, int32_t min_l, int32_t prune)
 {
     ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
     ovec L = {0}, R = {0}, P = {0}, Q = {0}, records = {0};
-    oacc acc = {0, 0, 0, 0, rec ? &records : NULL, 0, 0, NULL, 0, min_r, min_l};
+    oacc acc = {0, 0, 0, 0, rec ? &records : NULL, 0, 0, NULL, 0, min_r, min_l, prune ? 1 : 0};
     if (top_level(&g, &L, &P, min_l)) acc.err = 1;
     else mbea(&g, &L, &R, &P, &Q, &acc);
     ov_free(&L);
@@ -432,6 +532,9 @@ typedef struct {
     const int32_t *seq;
     const int64_t *pos;
     int64_t nseq;
+    const int64_t *rep;    /* pruned mode: twin_reps of the top-level sequence, else NULL */
+    const int32_t *kept;   /* pruned mode: the vertices of seq with rep[i] = i, in order */
+    const int64_t *nkept;  /* pruned mode: nkept[i] = how many of them sit before position i */
     const ovec *L;
     const int32_t *roots;
     int64_t nroots;
@@ -452,8 +555,22 @@ static void run_root(root_job *j, int64_t k)
     if (r < 0 || r >= j->g->nU || j->pos[r] < 0) return; /* isolated: never popped */
     int64_t i = j->pos[r];
     ovec R = {0};
-    oacc acc = {0, 0, 0, 0, NULL, 0, 0, NULL, 0, j->min_r, j->min_l};
-    mbea_iteration(j->g, j->L, &R, r, j->seq + i + 1, j->nseq - i - 1, j->seq, i, NULL, &acc);
+    oacc acc = {0, 0, 0, 0, NULL, 0, 0, NULL, 0, j->min_r, j->min_l, j->rep != NULL};
+    if (!j->rep) {
+        mbea_iteration(j->g, j->L, &R, r, j->seq + i + 1, j->nseq - i - 1, j->seq, i, NULL, &acc);
+    } else if (j->rep[i] == i) { /* a removed root is never popped */
+        int32_t *rest = (int32_t *)malloc((size_t)(j->nseq - i > 0 ? j->nseq - i : 1) * sizeof(int32_t));
+        if (!rest) {
+            j->err = 1;
+            return;
+        }
+        int64_t nr = 0;
+        for (int64_t t = i + 1; t < j->nseq; ++t)
+            if (j->rep[t] >= i) rest[nr++] = j->seq[t];
+        /* Q at this pop: the earlier roots that were popped */
+        mbea_iteration(j->g, j->L, &R, r, rest, nr, j->kept, j->nkept[i], NULL, &acc);
+        free(rest);
+    }
     o[0] = acc.count;
     o[1] = acc.hash;
     o[2] = acc.nodes;
@@ -479,19 +596,19 @@ static void *root_worker(void *arg)
  * Per-root results: out[4k..4k+3] = (count, hash, nodes, bytes) of the top-level
  * iteration whose candidate is roots[k] (zeros for a vertex that is never
  * popped), and out_b[k] (when out_b is not NULL) its bytes under the second
- * model; min_r, min_l: the size filter as in orc_enumerate.
- * Runs on nthreads POSIX threads. Returns 0 or -1.
+ * model; min_r, min_l, prune: as in orc_enumerate (a root removed by the
+ * pruning gives zeros). Runs on nthreads POSIX threads. Returns 0 or -1.
  */
 int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_adj, const int32_t *v_off,
                  const int32_t *v_adj, const int32_t *roots, int64_t nroots, uint64_t *out, int32_t nthreads,
-                 uint64_t *out_b, int32_t min_r, int32_t min_l)
+                 uint64_t *out_b, int32_t min_r, int32_t min_l, int32_t prune)
 {
     ograph g = {nU, nV, u_off, u_adj, v_off, v_adj};
     ovec L = {0}, P = {0};
     int rc = -1;
     okey *ord = NULL;
-    int32_t *seq = NULL;
-    int64_t *pos = NULL;
+    int32_t *seq = NULL, *kept = NULL;
+    int64_t *pos = NULL, *rep = NULL, *nkept = NULL;
     if (top_level(&g, &L, &P, min_l)) goto done;
     ord = (okey *)malloc((size_t)(P.n ? P.n : 1) * sizeof(okey));
     seq = (int32_t *)malloc((size_t)(P.n ? P.n : 1) * sizeof(int32_t));
@@ -510,11 +627,26 @@ int orc_per_root(int32_t nU, int32_t nV, const int32_t *u_off, const int32_t *u_
         seq[i] = ord[i].id;
         pos[seq[i]] = i;
     }
+    if (prune) {
+        rep = (int64_t *)malloc((size_t)(P.n ? P.n : 1) * sizeof(int64_t));
+        kept = (int32_t *)malloc((size_t)(P.n ? P.n : 1) * sizeof(int32_t));
+        nkept = (int64_t *)malloc((size_t)(P.n + 1) * sizeof(int64_t));
+        if (!rep || !kept || !nkept || twin_reps(&g, &L, seq, P.n, rep)) goto done;
+        int64_t nk = 0;
+        for (int64_t i = 0; i < P.n; ++i) {
+            nkept[i] = nk;
+            if (rep[i] == i) kept[nk++] = seq[i];
+        }
+        nkept[P.n] = nk;
+    }
     root_job job;
     job.g = &g;
     job.seq = seq;
     job.pos = pos;
     job.nseq = P.n;
+    job.rep = rep;
+    job.kept = kept;
+    job.nkept = nkept;
     job.L = &L;
     job.roots = roots;
     job.nroots = nroots;
@@ -545,6 +677,9 @@ done:
     free(ord);
     free(seq);
     free(pos);
+    free(rep);
+    free(kept);
+    free(nkept);
     return rc;
 }
 
@@ -596,7 +731,7 @@ static void *batch_worker(void *arg)
         const int32_t *uo = j->u_off + j->u_off_start[gi];
         const int32_t *vo = j->v_off + j->v_off_start[gi];
         if (orc_enumerate(j->nU[gi], j->nV[gi], uo, j->u_adj + e0, vo, j->v_adj + e0, j->out + 4 * (int64_t)gi,
-                          NULL, NULL, NULL, 1, 1))
+                          NULL, NULL, NULL, 1, 1, 0))
             j->err = 1;
     }
     return NULL;

@@ -6,7 +6,9 @@
 - an independent brute-force closure enumerator on >= 1,000 random graphs,
   itself pinned by the crown graph's 2^n - 2;
 - invariants: closure of every emitted pair, side swap, relabelling,
-  per-root decomposition.
+  per-root decomposition;
+- the pruned mode (iMBE's L - L' removal) against its own hand traces, a
+  closed form (disjoint twin blocks) and the plain mode's biclique sets.
 """
 import json
 import os
@@ -292,3 +294,77 @@ def test_size_filter_hand_trace():
     # three roots are popped (three nodes), none has a child
     c, h, n, b, rec = oracle.enumerate_graph(g, records=True, min_r=2)
     assert H.canon(rec) == [((0, 1), (0,)), ((1, 2), (1,))] and n == 3
+
+
+# ------------------------------------------------------ pruned mode (iMBE)
+
+def test_prune_hand_traces(golden_dir):
+    with open(os.path.join(golden_dir, "prune_traces.json")) as f:
+        traces = json.load(f)["traces"]
+    for t in traces:
+        g = H.graph(t["nU"], t["nV"], t["edges"])
+        expect = H.canon([(tuple(r), tuple(l)) for r, l in t["bicliques"]])
+        c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
+        assert (c, n, b) == (t["count"], t["plain_nodes"], t["plain_bytes"]), t["name"]
+        assert H.canon(rec) == expect
+        c, h, n, b, rec = oracle.enumerate_graph(g, records=True, prune=True)
+        assert (c, n, b) == (t["count"], t["pruned_nodes"], t["pruned_bytes"]), t["name"]
+        assert H.canon(rec) == expect and h == sm_hash(expect)
+        # the per-root driver prunes the top level the same way
+        pr = oracle.per_root(g, prune=True)
+        assert (int(pr[:, 0].sum()), int(pr[:, 2].sum()), int(pr[:, 3].sum())) == (c, n, b)
+        assert sum(int(x) for x in pr[:, 1]) & MASK == h
+
+
+@pytest.mark.parametrize("k,a,b", [(1, 5, 3), (3, 4, 2), (6, 1, 7), (2, 9, 9)])
+def test_prune_twin_blocks_closed_form(k, a, b):
+    # k disjoint copies of K_{a,b}: the a vertices of a block are twins, so
+    # only the first of each block is popped (plain: all k*a are)
+    g = H.complete(a, b)
+    for _ in range(k - 1):
+        g = H.disjoint_union(g, H.complete(a, b))
+    assert oracle.enumerate_graph(g)[2] == k * a
+    c, h, n, _ = oracle.enumerate_graph(g, prune=True)
+    assert (c, n) == (k, k)
+
+
+@pytest.mark.parametrize("n", [2, 5, 9])
+def test_prune_no_twins_changes_nothing(n):
+    # matching and crown graphs: no two U vertices share a neighbourhood in
+    # any level set the search meets on the matching; the crown's top level
+    # has none either
+    g = H.matching(n)
+    assert oracle.enumerate_graph(g, prune=True) == oracle.enumerate_graph(g)
+    c, h, _, _ = oracle.enumerate_graph(H.crown(n), prune=True)
+    assert c == 2 ** n - 2
+
+
+def test_prune_same_bicliques_fewer_nodes_random():
+    rng = np.random.default_rng(1401)
+    fewer = 0
+    for trial in range(400):
+        nU = int(rng.integers(1, 13))
+        nV = int(rng.integers(1, 30))
+        p = float(rng.choice([0.1, 0.3, 0.5, 0.8]))
+        g = H.random_graph(rng, nU, nV, p)
+        c0, h0, n0, b0, rec0 = oracle.enumerate_graph(g, records=True)
+        c1, h1, n1, b1, rec1 = oracle.enumerate_graph(g, records=True, prune=True)
+        assert (c1, h1) == (c0, h0) and H.canon(rec1) == H.canon(rec0), trial
+        assert H.canon(rec1) == H.canon(oracle.bruteforce(g, records=True)[2]), trial
+        assert n1 <= n0 and b1 <= b0, trial
+        fewer += n1 < n0
+        # whole run = sum of its roots, pruned too
+        pr = oracle.per_root(g, prune=True)
+        assert int(pr[:, 0].sum()) == c1 and int(pr[:, 2].sum()) == n1 and int(pr[:, 3].sum()) == b1, trial
+        assert (int(pr[:, 1].sum()) & MASK) == h1, trial
+    assert fewer > 50
+
+
+@pytest.mark.parametrize("min_r,min_l", [(2, 1), (1, 3), (2, 2)])
+def test_prune_with_size_filter(min_r, min_l):
+    rng = np.random.default_rng(99)
+    for trial in range(60):
+        g = H.random_graph(rng, int(rng.integers(2, 12)), int(rng.integers(2, 25)), 0.4)
+        a = oracle.enumerate_graph(g, records=True, min_r=min_r, min_l=min_l)
+        b = oracle.enumerate_graph(g, records=True, min_r=min_r, min_l=min_l, prune=True)
+        assert a[:2] == b[:2] and H.canon(a[4]) == H.canon(b[4]) and b[2] <= a[2], trial
