@@ -42,7 +42,8 @@ WORKLOAD_DESC = ("Chung-Lu bipartite |U|=20,000 |V|=50,000 |E|=200,000 exponents
 # sources it was taken on; a kernel changed since then reports null.
 TRAFFIC = {"bytes": 85569210112 + 109905536256,
            "sources_sha256": "ddc9fef3b3d927ec8e10651eed26705b57d8d24836dbf5a8e4812586533e522c"}
-KERNEL_SOURCES = ("csrc/mbe_search.cu", "csrc/mbe_internal.h", "csrc/mbe_bits.h")
+KERNEL_SOURCES = ("csrc/mbe_search.cu", "csrc/mbe_internal.h", "csrc/mbe_bits.h", "csrc/mbe_emit.cuh",
+                  "csrc/mbe_list.cuh", "csrc/mbe_twins.cuh")
 
 
 def kernel_sources_sha256():
@@ -270,13 +271,49 @@ def measure_batched(m, torch, tune=False):
             row["tuned"] = {"block_threads": t.block_threads, "blocks_per_sm": t.blocks_per_sm, "steal": t.steal,
                             "layout": t.layout, "sample_ms": t.tuned_ms, "default_sample_ms": t.default_ms}
         classes.append(row)
-    return {"workload": f"batch4096: all {n} graphs in one call ({tot.count} bicliques)",
+    return {"workload": f"batch4096: all {n} graphs in one call ({tot.count} bicliques)", "count": int(tot.count),
             "batched_ms": tot.device_ms, "batched_ms_per_graph": tot.device_ms / n,
             "batched_bicliques_per_s": tot.count / (tot.device_ms * 1e-3),
             "plain_ms": plain_ms, "plain_ms_per_graph": plain_ms / n,
             "plain_bicliques_per_s": tot.count / (plain_ms * 1e-3),
             "speedup_batched_over_plain": plain_ms / tot.device_ms, "autotune_seconds": tune_s,
             "per_class": classes}
+
+
+def measure_pruned(m, torch, batch_ms=None, batch_count=None):
+    """The pruned search (iMBE's L - L' removal, Section II-C) against the plain one.
+
+    Same bicliques (count and hash checked equal), fewer nodes. Single graphs:
+    best of three device times per form; the batch: one pruned
+    mbe_enumerate_batch call over all 4,096 graphs against the batched plain
+    call timed in the batched form.
+    """
+    import synth
+    out = {}
+    for name in ("chunglu20k", "planted5k", "chunglu200k"):
+        g = synth.workload(name)
+        G = m.Graph.from_synth(g)
+        res = {}
+        for prune in (0, 1):
+            G.enumerate(prune=prune)  # warm-up (twin classes, workspace)
+            runs = [G.enumerate(prune=prune) for _ in range(3)]
+            best = min(runs, key=lambda r: r.device_ms)
+            res[prune] = best
+        G.close()
+        p, q = res[0], res[1]
+        assert (p.count, p.hash) == (q.count, q.hash), name
+        out[name] = {"plain_ms": p.device_ms, "pruned_ms": q.device_ms, "speedup": p.device_ms / q.device_ms,
+                     "count": int(q.count), "plain_nodes": int(p.nodes), "pruned_nodes": int(q.nodes),
+                     "pruned_bicliques_per_s": q.count / (q.device_ms * 1e-3),
+                     "plain_bytes_alg": int(p.bytes_alg), "pruned_bytes_alg": int(q.bytes_alg)}
+    gs = [synth.batch_graph(3 + i) for i in range(4096)]
+    per, tot = m.enumerate_batch(synth.pack(gs), prune=1)
+    assert tot.status == 0 and (batch_count is None or tot.count == batch_count)
+    out["batch4096"] = {"pruned_ms": tot.device_ms, "pruned_ms_per_graph": tot.device_ms / len(gs),
+                        "pruned_bicliques_per_s": tot.count / (tot.device_ms * 1e-3), "count": int(tot.count),
+                        "pruned_nodes": int(tot.nodes), "batched_plain_ms": batch_ms,
+                        "speedup_over_batched_plain": (batch_ms / tot.device_ms) if batch_ms else None}
+    return out
 
 
 def measure_learned(m, torch):
@@ -435,7 +472,10 @@ def run_mbe(args):
     l2_gbs = m.copy_bandwidth(32 * 1024 * 1024, iters=10)
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:
-        forms = {"batched": measure_batched(m, torch, tune=args.tune), "learned": measure_learned(m, torch)}
+        batched = measure_batched(m, torch, tune=args.tune)
+        forms = {"batched": batched, "learned": measure_learned(m, torch),
+                 "pruned": measure_pruned(m, torch, batch_ms=batched["batched_ms"],
+                                          batch_count=batched["count"])}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         runs = sorted((cpu_oracle_sample(g) for _ in range(3)), key=lambda d: d["seconds"])

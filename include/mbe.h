@@ -208,6 +208,14 @@ typedef struct {
                                  |R'| + |P'| >= min_r, a candidate reaching fewer than min_l vertices of
                                  L' does not enter P', and a root of degree below min_l is never popped
                                  (nodes and bytes_alg count what was searched) */
+    int32_t prune;            /* 1 = embedded pruning by L - L' removal (iMBE, Sec. II-C): a candidate
+                                 whose neighbourhood in L equals that of a candidate popped before it
+                                 leaves P at that pop (whether or not that node is maximal) and joins
+                                 neither P' nor Q'. Same bicliques, fewer nodes; nodes and bytes_alg
+                                 count the pruned search. Both layouts and mbe_enumerate_batch; bitset
+                                 level sets only (MBE_ERR_UNSUPPORTED for a graph with a root above the
+                                 bitset limit); 0 = off. The first pruned call on a graph computes its
+                                 top-level twin classes (kept with the graph) */
 } mbe_options;
 
 /* Fill *opt with the defaults (all "auto"). */

@@ -4,6 +4,8 @@ Calls only ``oracle`` and the input generators in ``synth``; nothing here
 touches the GPU library. Usage:
 
     python oracle/make_golden.py er200x300 planted5k chunglu20k chunglu200k batch4096 [--threads N]
+    python oracle/make_golden.py planted5k --prune [--threads N]
+
 
 Each workload writes ``tests/golden/<name>.json`` with the graph digest (so a
 machine that draws a different graph is caught before parity is checked),
@@ -80,6 +82,18 @@ def whole_graph(name, g, threads, n_heavy=16, n_random=48, records=False):
         c, h, n, b, rec = oracle.enumerate_graph(g, records=True)
         assert c == out["total"]["count"] and hex(h) == out["total"]["hash"]
         out["set_sha256"] = set_digest(rec)
+    return out
+
+
+def whole_graph_pruned(name, g, threads, n_heavy=16, n_random=48):
+    """The pruned mode (iMBE's L - L' removal): whole-graph total and per-root rows."""
+    t0 = time.time()
+    pr = oracle.per_root(g, nthreads=threads, prune=True)
+    out = {"workload": name, "mode": "pruned", "graph": _graph_info(g),
+           "total": _row(pr.sum(axis=0, dtype=np.uint64)), "oracle_seconds": round(time.time() - t0, 1),
+           "oracle_threads": threads}
+    roots = _sample_roots(g, pr, n_heavy, n_random, seed=len(name) + 1)
+    out["per_root"] = {str(r): _row(pr[r]) for r in roots}
     return out
 
 
@@ -239,6 +253,7 @@ def main():
     ap.add_argument("--prefix", action="store_true", help="resumable seeded-order per-root run (large graphs)")
     ap.add_argument("--progress", default=None, help="progress file for --prefix")
     ap.add_argument("--budget", type=float, default=None, help="seconds to spend in this --prefix invocation")
+    ap.add_argument("--prune", action="store_true", help="the pruned mode: writes <name>_prune.json")
     ap.add_argument("--batch-rest", action="store_true",
                     help="add per-root rows of the batch graphs without whole-graph rows to batch4096.json")
     args = ap.parse_args()
@@ -249,7 +264,11 @@ def main():
         return
     for name in args.names:
         t0 = time.time()
-        if args.prefix:
+        suffix = ""
+        if args.prune:
+            out = whole_graph_pruned(name, synth.workload(name), args.threads)
+            suffix = "_prune"
+        elif args.prefix:
             out = prefix_sample(name, synth.workload(name), args.threads, progress=args.progress,
                                 time_budget=args.budget)
         elif name == "er200x300":
@@ -262,7 +281,7 @@ def main():
             out = batch(name, args.threads)
         else:
             raise SystemExit(f"unknown workload {name}")
-        path = os.path.join(GOLDEN, f"{name}.json")
+        path = os.path.join(GOLDEN, f"{name}{suffix}.json")
         with open(path, "w") as f:
             json.dump(out, f, indent=1, sort_keys=True)
         print(f"{name}: wrote {path} in {time.time() - t0:.1f}s", flush=True)

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmbe.so")
-SOURCES = ["mbe_search.cu", "mbe_search_lists.cu", "mbe_search_rows.cu", "mbe_search_rows_lists.cu", "mbe_prep.cu", "mbe_host.cu", "mbe_batch.cu", "mbe_learn.cu", "mbe_copy.cu", "mbe_noalloc.cu"]
+SOURCES = ["mbe_search.cu", "mbe_search_lists.cu", "mbe_search_prune.cu", "mbe_search_rows.cu", "mbe_search_rows_lists.cu", "mbe_search_rows_prune.cu", "mbe_prep.cu", "mbe_host.cu", "mbe_batch.cu", "mbe_learn.cu", "mbe_copy.cu", "mbe_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

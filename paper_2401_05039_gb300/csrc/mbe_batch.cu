@@ -40,6 +40,8 @@ struct DeviceBatch {
     int64_t n_tasks_cap = 0;
     std::vector<unsigned long long> hb;    // host copy of gbounds
     int32_t max_nU = 1;
+    int64_t n_uoff = 0;                    // entries of the concatenated u_off
+    int32_t *trep = nullptr;               // [n_uoff] twin classes of the pruned search (on request)
 
     void release()
     {
@@ -53,6 +55,7 @@ struct DeviceBatch {
         cudaFree(owner);
         cudaFree(ctls);
         cudaFree(tasks);
+        cudaFree(trep);
         *this = DeviceBatch();
     }
 };
@@ -89,6 +92,7 @@ int upload(const HostBatch &b, DeviceBatch &d, cudaStream_t s)
     }
     const size_t eb = sizeof(int32_t) * (size_t)std::max<int64_t>(nE, 1);
     d.n_tasks_cap = std::max<int64_t>(n_tasks, 1);
+    d.n_uoff = n_uoff;
     if (cudaMalloc(&d.uo, sizeof(int32_t) * (size_t)n_uoff) != cudaSuccess ||
         cudaMalloc(&d.vo, sizeof(int32_t) * (size_t)n_voff) != cudaSuccess || cudaMalloc(&d.ua, eb) != cudaSuccess ||
         cudaMalloc(&d.va, eb) != cudaSuccess || cudaMalloc(&d.bad, sizeof(int32_t)) != cudaSuccess ||
@@ -289,6 +293,9 @@ int run_classes(DeviceBatch &d, std::vector<ClassPlan> &plans, const std::vector
             a.min_r = std::max(1, o.min_r);
             a.min_l = std::max(1, o.min_l);
             a.lists = (a.min_r > 1 || a.min_l > 1) ? 1 : 0; // the size filter runs in the extended variant
+            a.prune = d.trep ? 1 : 0;                      // the pruned variant carries the filter too
+            a.trep = d.trep;
+            if (a.prune) a.lists = 0;
             a.per_task_owner = d.owner;
             a.per_root_mode = 2;
             a.emit = 0;
@@ -413,12 +420,25 @@ int mbe_enumerate_batch(int32_t n_graphs, const int64_t *edge_off, const int32_t
     mbe_default_options(&o);
     if (opts) o = *opts;
     if (o.layout < 0 || o.layout > kLayoutColumns) return set_status(total, MBE_ERR_INVALID_ARG);
+    if (o.prune < 0 || o.prune > 1) return set_status(total, MBE_ERR_INVALID_ARG);
     const mbe_class_params *tab = static_cast<const mbe_class_params *>(o.class_params);
     for (int k = 0; tab && k < MBE_N_CLASSES; ++k)
         if (tab[k].valid && (tab[k].layout < 0 || tab[k].layout > kLayoutColumns)) return set_status(total, MBE_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     DeviceBatch d;
     st = upload(b, d, s);
+    if (st == MBE_OK && o.prune) {
+        // the pruned search: twin classes of every graph (the batch keeps
+        // every degree within the bitset limit, so no list path is needed)
+        if (cudaMalloc(&d.trep, sizeof(int32_t) * (size_t)std::max<int64_t>(d.n_uoff, 1)) != cudaSuccess) {
+            cudaGetLastError();
+            d.trep = nullptr;
+            st = MBE_ERR_OOM;
+        } else {
+            cudaError_t e = twin_classes(d.desc, n_graphs, d.max_nU, d.n_uoff, d.uo, d.ua, d.trep, s);
+            if (e != cudaSuccess) st = cuda_status(e);
+        }
+    }
     if (st != MBE_OK) {
         d.release();
         return set_status(total, st);

@@ -35,6 +35,7 @@ struct mbe_graph {
     int32_t *task_root = nullptr;    // [nU + 32 * kSplitHead] tasks of the learned schedule
     int32_t *task_split = nullptr;
     int32_t *bad = nullptr;
+    int32_t *trep = nullptr;         // [nU + 1] top-level twin classes of the pruned search (first use)
 };
 
 namespace mbe {
@@ -298,6 +299,10 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         a.min_l = std::max(1, o.min_l);
         // the extended kernel variant: some root needs the sorted-list path, or a size filter is set
         a.lists = (in.max_deg > 64 * a.max_words || a.min_r > 1 || a.min_l > 1) ? 1 : 0;
+        // the pruned variant carries the size filter too (and no list path)
+        a.prune = in.prune;
+        a.trep = in.trep;
+        if (a.prune) a.lists = 0;
         a.totals = ws.ctl->totals;
         a.per_task_owner = in.per_owner;
         a.per_root_mode = in.per_mode;
@@ -560,6 +565,7 @@ int mbe_graph_destroy(mbe_graph *g)
     cudaFree(g->order_l);
     cudaFree(g->task_root);
     cudaFree(g->task_split);
+    cudaFree(g->trep);
     cudaFree(g->bad);
     delete g;
     return MBE_OK;
@@ -717,7 +723,8 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
                    bicliques->capacity_bicliques < 0))
         return set_status(out, MBE_ERR_INVALID_ARG);
     if (o.block_threads < 0 || o.blocks_per_sm < 0 || o.watchdog_ms < 0 || o.arena_bytes < 0 || o.layout < 0 ||
-        o.layout > kLayoutColumns || o.bitset_max_words < 0 || o.min_r < 0 || o.min_l < 0)
+        o.layout > kLayoutColumns || o.bitset_max_words < 0 || o.min_r < 0 || o.min_l < 0 || o.prune < 0 ||
+        o.prune > 1)
         return set_status(out, MBE_ERR_INVALID_ARG);
     cudaStream_t s = (cudaStream_t)stream;
     if (g->nU == 0 || g->n_live == 0) return set_status(out, MBE_OK);
@@ -770,6 +777,25 @@ int mbe_enumerate(const mbe_graph *gc, const mbe_options *opts, void *stream, mb
     in.per_mode = 1;
     in.layout = resolve_layout(o.layout, g->max_deg_v);
     in.max_deg = g->max_deg_u;
+    if (o.prune) {
+        const int32_t mw = o.bitset_max_words > 0 ? std::min(o.bitset_max_words, kMaxBitsetWords) : kMaxBitsetWords;
+        if (g->max_deg_u > 64 * mw) return set_status(out, MBE_ERR_UNSUPPORTED);
+        if (!g->trep) {
+            if (cudaMalloc(&g->trep, sizeof(int32_t) * (size_t)(g->nU + 1)) != cudaSuccess) {
+                cudaGetLastError();
+                g->trep = nullptr;
+                return set_status(out, MBE_ERR_OOM);
+            }
+            cudaError_t te = twin_classes(g->d_desc, 1, g->nU, (int64_t)g->nU + 1, g->u_off, g->u_adj, g->trep, s);
+            if (te != cudaSuccess) {
+                cudaFree(g->trep);
+                g->trep = nullptr;
+                return set_status(out, cuda_status(te));
+            }
+        }
+        in.prune = 1;
+        in.trep = g->trep;
+    }
     int st = run_search(device_workspace(), in, o, s, out, bicliques);
     if (out) out->prep_ms = prep_ms;
     return set_status(out, st);

@@ -57,6 +57,9 @@ struct SearchArgs {
     int32_t lists;        // 1: launch the extended variant (some root exceeds the bitset limit, or a size
                           // filter is set)
     int32_t min_r, min_l; // size filter: only bicliques with |R| >= min_r and |L| >= min_l (1, 1 = all)
+    int32_t prune;        // 1: launch the pruned variant (iMBE's L - L' removal, Section II-C)
+    const int32_t *trep;  // pruned variant: per graph, at its u_off base, [nU] smallest local U id with the
+                          // same neighbourhood (itself if none)
 
     // outputs
     unsigned long long *totals;   // [8]: count, hash, nodes, bytes, donations, steals, -, -
@@ -108,8 +111,10 @@ constexpr int kMaxBitsetWords = 32;
 // Upper bound of the largest frame below a root of degree d with at most nc
 // candidates. A bitset frame (level set of w <= 64 * kMaxBitsetWords
 // vertices): header, L ids, X columns (w x ceil(nc/64) words), P ids, P
-// rows (32-row tiles of ceil(w/64) words), R ids. A list frame (a wider
-// level set): header, L ids, Q ids, P ids, R ids.
+// rows (32-row tiles of ceil(w/64) words), the pruned variant's twin
+// positions (one int32 per P entry) and removal mask (one bit per X
+// position), R ids. A list frame (a wider level set): header, L ids, Q ids,
+// P ids, R ids.
 #if defined(__CUDACC__)
 __host__ __device__
 #endif
@@ -119,7 +124,7 @@ inline int64_t level1_frame_bound(int64_t d, int64_t nc)
     const int64_t w = d < 64 * kMaxBitsetWords ? d : 64 * kMaxBitsetWords;
     const int64_t W = (w + 63) / 64;
     const int64_t bits = kFrameHdrBytes + p16(4 * w) + p16(8 * w * ((nc + 63) / 64)) + p16(4 * nc) +
-                         256 * W * ((nc + 31) / 32) + p16(4 * (nc + 1));
+                         256 * W * ((nc + 31) / 32) + p16(4 * nc) + p16(8 * ((nc + 63) / 64)) + p16(4 * (nc + 1));
     const int64_t list = kFrameHdrBytes + p16(4 * d) + 2 * p16(4 * nc) + p16(4 * (nc + 1));
     return d > w && list > bits ? list : bits;
 }
@@ -146,18 +151,26 @@ int search_smem_per_warp();
 cudaError_t launch_search_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
 int search_lists_fit_shape(int threads, int blocks_per_sm_req);
 
+// The column-layout kernel's pruned variant (mbe_search_prune.cu), bitset
+// level sets only; launch_search dispatches to it when args.prune.
+cudaError_t launch_search_prune(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
+int search_prune_fit_shape(int threads, int blocks_per_sm_req);
+
 // Resident blocks per SM for a block of `threads` threads, at most
 // blocks_per_sm_req; a negative value -t means `threads` exceeds the
 // kernel's limit and t is the largest allowed block size.
 int search_fit_shape(int threads, int blocks_per_sm_req);
 
 // The same three for the row-layout search kernel (mbe_search_rows.cu),
-// and its list-path variant (mbe_search_rows_lists.cu).
+// its list-path variant (mbe_search_rows_lists.cu) and its pruned variant
+// (mbe_search_rows_prune.cu).
 cudaError_t launch_search_rows(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
 int search_rows_smem_per_warp();
 int search_rows_fit_shape(int threads, int blocks_per_sm_req);
 cudaError_t launch_search_rows_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
 int search_rows_lists_fit_shape(int threads, int blocks_per_sm_req);
+cudaError_t launch_search_rows_prune(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);
+int search_rows_prune_fit_shape(int threads, int blocks_per_sm_req);
 
 // Frame layouts of the two search kernels.
 enum : int32_t { kLayoutAuto = 0, kLayoutRows = 1, kLayoutColumns = 2 };

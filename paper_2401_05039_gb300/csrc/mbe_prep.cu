@@ -1,5 +1,6 @@
 // Preprocessing kernels: input validation, per-root workspace bounds and the
 // static execution order of the roots.
+#include "mbe_bits.h"
 #include "mbe_internal.h"
 #include "mbe_prep.h"
 
@@ -267,6 +268,82 @@ __global__ void max_degree_kernel(const int32_t *off, int32_t n, int32_t *out)
     atomicMax(out, m);
 }
 
+// Top-level twin classes for the pruned search: U vertices of one graph
+// with the same neighbourhood. A digest of (graph, degree, sorted list)
+// keys an open-addressing table (2^k >= 2 entries per vertex, linear
+// probing) that keeps the smallest index of each key; every vertex then
+// compares its list with that vertex's list, so a digest collision only
+// costs pruning (the vertex keeps itself as representative), never a
+// wrong removal. Indices are those of the concatenated u_off (graph base +
+// local id), one grid row per graph.
+__device__ __forceinline__ unsigned long long twin_digest(int g, const int32_t *adj, int d)
+{
+    unsigned long long h = splitmix(((unsigned long long)(uint32_t)g << 32) | (unsigned long long)(uint32_t)d);
+    for (int k = 0; k < d; ++k) h = splitmix(h ^ (unsigned long long)(uint32_t)adj[k]);
+    return h | 1ULL; // 0 marks an empty slot
+}
+
+__global__ void twin_fill_kernel(int32_t *minid, int64_t T)
+{
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < T; t += (int64_t)gridDim.x * blockDim.x)
+        minid[t] = 0x7fffffff;
+}
+
+__global__ void twin_insert_kernel(const GraphDesc *graphs, int32_t n_graphs, const int32_t *u_off_cat,
+                                   const int32_t *u_adj_cat, unsigned long long *keys, int32_t *minid, int64_t T,
+                                   int32_t *slot_of)
+{
+    const int g = blockIdx.y;
+    if (g >= n_graphs) return;
+    const GraphDesc G = graphs[g];
+    const int32_t *u_off = u_off_cat + G.u_off_base;
+    const int32_t *u_adj = u_adj_cat + G.edge_base;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < G.nU; u += gridDim.x * blockDim.x) {
+        const int64_t p = G.u_off_base + u;
+        const int o = u_off[u], d = u_off[u + 1] - o;
+        slot_of[p] = -1;
+        if (d == 0) continue;
+        const unsigned long long h = twin_digest(g, u_adj + o, d);
+        int64_t slot = (int64_t)(h & (unsigned long long)(T - 1));
+        for (int64_t t = 0; t < T; ++t) { // fewer keys than T / 2: a free slot is always found
+            const unsigned long long prev = atomicCAS(keys + slot, 0ULL, h);
+            if (prev == 0ULL || prev == h) {
+                atomicMin(minid + slot, (int32_t)p);
+                slot_of[p] = (int32_t)slot;
+                break;
+            }
+            slot = (slot + 1) & (T - 1);
+        }
+    }
+}
+
+__global__ void twin_rep_kernel(const GraphDesc *graphs, int32_t n_graphs, const int32_t *u_off_cat,
+                                const int32_t *u_adj_cat, const int32_t *minid, const int32_t *slot_of,
+                                int32_t *trep)
+{
+    const int g = blockIdx.y;
+    if (g >= n_graphs) return;
+    const GraphDesc G = graphs[g];
+    const int32_t *u_off = u_off_cat + G.u_off_base;
+    const int32_t *u_adj = u_adj_cat + G.edge_base;
+    for (int u = blockIdx.x * blockDim.x + threadIdx.x; u < G.nU; u += gridDim.x * blockDim.x) {
+        const int64_t p = G.u_off_base + u;
+        int r = u;
+        if (slot_of[p] >= 0) {
+            const int64_t cp = minid[slot_of[p]];
+            const int64_t c = cp - G.u_off_base; // a local id when the vertex is of this graph
+            if (c >= 0 && c < u) {
+                const int o = u_off[u], d = u_off[u + 1] - o;
+                const int oc = u_off[c], dc = u_off[c + 1] - oc;
+                bool same = dc == d;
+                for (int k = 0; same && k < d; ++k) same = u_adj[o + k] == u_adj[oc + k];
+                if (same) r = (int)c;
+            }
+        }
+        trep[p] = r;
+    }
+}
+
 } // namespace
 
 cudaError_t validate_batch(const GraphDesc *d_graphs, int32_t n_graphs, const int32_t *u_off, const int32_t *u_adj,
@@ -357,6 +434,37 @@ cudaError_t order_by_key_desc(const int32_t *d_key, int32_t n, int32_t max_key, 
     scan_desc_kernel<<<1, 1024, 0, s>>>(d_hist, max_key + 1);
     key_scatter_kernel<<<blocks, 256, 0, s>>>(d_key, n, d_hist, d_order);
     return cudaGetLastError();
+}
+
+cudaError_t twin_classes(const GraphDesc *d_graphs, int32_t n_graphs, int32_t max_nU, int64_t n_uoff,
+                         const int32_t *u_off, const int32_t *u_adj, int32_t *d_trep, cudaStream_t s)
+{
+    if (n_uoff >= 0x7fffffffLL) return cudaErrorInvalidValue; // indices are int32
+    int64_t T = 2;
+    while (T < 2 * n_uoff) T <<= 1;
+    unsigned long long *keys = nullptr;
+    int32_t *minid = nullptr, *slot_of = nullptr;
+    cudaError_t e = cudaMalloc(&keys, sizeof(unsigned long long) * (size_t)T);
+    if (e == cudaSuccess) e = cudaMalloc(&minid, sizeof(int32_t) * (size_t)T);
+    if (e == cudaSuccess) e = cudaMalloc(&slot_of, sizeof(int32_t) * (size_t)std::max<int64_t>(n_uoff, 1));
+    if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * (size_t)T, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(slot_of, 0xff, sizeof(int32_t) * (size_t)std::max<int64_t>(n_uoff, 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_trep, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(n_uoff, 1), s);
+    if (e == cudaSuccess) {
+        const int fill = (int)std::min<int64_t>((T + 255) / 256, 4 * 152);
+        int gx = (max_nU + 255) / 256;
+        gx = std::max(1, std::min(gx, 64));
+        const dim3 grid(gx, n_graphs);
+        twin_fill_kernel<<<fill, 256, 0, s>>>(minid, T);
+        twin_insert_kernel<<<grid, 256, 0, s>>>(d_graphs, n_graphs, u_off, u_adj, keys, minid, T, slot_of);
+        twin_rep_kernel<<<grid, 256, 0, s>>>(d_graphs, n_graphs, u_off, u_adj, minid, slot_of, d_trep);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(keys);
+    cudaFree(minid);
+    cudaFree(slot_of);
+    return e;
 }
 
 } // namespace mbe

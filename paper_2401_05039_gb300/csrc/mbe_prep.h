@@ -39,4 +39,12 @@ cudaError_t degree_larger(const int32_t *u_off, int32_t nU, int32_t max_deg, int
 cudaError_t order_by_key_desc(const int32_t *d_key, int32_t n, int32_t max_key, int32_t *d_hist, int32_t *d_order,
                               cudaStream_t s);
 
+// Top-level twin classes of the pruned search, for every graph of a
+// (possibly one-graph) batch: d_trep[u_off_base + u] = the smallest local U
+// id of the graph whose neighbourhood equals N(u) (u itself when there is
+// none, and for an isolated u). n_uoff = entries of the concatenated u_off
+// (d_trep has as many). Allocates and frees its own table; synchronises s.
+cudaError_t twin_classes(const GraphDesc *d_graphs, int32_t n_graphs, int32_t max_nU, int64_t n_uoff,
+                         const int32_t *u_off, const int32_t *u_adj, int32_t *d_trep, cudaStream_t s);
+
 } // namespace mbe

@@ -68,6 +68,8 @@ struct RunInput {
     int32_t per_mode;
     int32_t layout = kLayoutColumns; // resolved frame layout (kLayoutRows / kLayoutColumns)
     int32_t max_deg = 0;             // largest U degree of the graphs searched
+    int32_t prune = 0;               // the pruned variant (single graphs, bitset level sets)
+    const int32_t *trep = nullptr;   // its top-level twin classes ([nU])
 };
 
 

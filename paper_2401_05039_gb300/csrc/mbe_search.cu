@@ -39,16 +39,28 @@
 #include "mbe_bits.h"
 #include "mbe_emit.cuh"
 #include "mbe_internal.h"
+#include "mbe_twins.cuh"
 
 // MBE_LIST_PATH = 1 builds the variant with the sorted-list path for level
 // sets wider than the bitset limit (mbe_search_lists.cu); it is launched only
-// for graphs with such roots. The list path's out-of-line calls would cost
-// the plain variant registers, hence two translation units.
+// for graphs with such roots. MBE_PRUNE = 1 builds the pruned variant
+// (mbe_search_prune.cu: iMBE's L - L' removal, bitset level sets only). The
+// out-of-line calls and extra state of either would cost the plain variant
+// registers, hence separate translation units.
 #ifndef MBE_LIST_PATH
 #define MBE_LIST_PATH 0
 #endif
-#if MBE_LIST_PATH
+#ifndef MBE_PRUNE
+#define MBE_PRUNE 0
+#endif
+#if MBE_PRUNE
+#define MBE_SEARCH_KERNEL search_prune_kernel
+#define MBE_VARIANT_FIT search_prune_fit_shape
+#define MBE_VARIANT_LAUNCH launch_search_prune
+#elif MBE_LIST_PATH
 #define MBE_SEARCH_KERNEL search_lists_kernel
+#define MBE_VARIANT_FIT search_lists_fit_shape
+#define MBE_VARIANT_LAUNCH launch_search_lists
 #else
 #define MBE_SEARCH_KERNEL search_kernel
 #endif
@@ -56,8 +68,11 @@
 namespace mbe {
 namespace {
 
-// The extended variant (MBE_LIST_PATH = 1) also carries the size filter.
-constexpr bool kExt = MBE_LIST_PATH != 0;
+// The extended variants (list path, pruning) also carry the size filter.
+constexpr bool kExt = MBE_LIST_PATH != 0 || MBE_PRUNE != 0;
+// The pruned variant: every frame carries, per P entry, the first position
+// of its twin class (rep, see twin_reps) and a removal mask over X.
+constexpr bool kPrune = MBE_PRUNE != 0;
 
 constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
@@ -127,14 +142,23 @@ struct Frame {
     uint64_t *Q;     // [m][QW] columns over X = Q then P (nQ + nP positions)
     int32_t *gid;    // [nP] P candidate ids (U side)
     uint64_t *rows;  // [ceil(nP/32)][W][32] P rows
+    int32_t *rep;    // pruned variant: [nP] first P position with the same row (see twin_reps)
+    uint64_t *dup;   // pruned variant: [QW] bit qpos + j set when rep[j] < j
     int32_t *R;      // [nR]
 };
+
+// Bytes of the pruned variant's twin sections (none in the other variants).
+__device__ __forceinline__ int64_t twin_bytes(int nP, int QW)
+{
+    return kPrune ? pad16(4LL * nP) + pad16(8LL * QW) : 0;
+}
 
 __device__ __forceinline__ int64_t frame_bytes(int m, int QW, int nP, int W, int nR)
 {
     int64_t tiles = (nP + 31) >> 5;
     // every section is a multiple of 16 bytes: frames are copied with 16-byte accesses
-    return kFrameHdrBytes + pad16(4LL * m) + pad16(8LL * m * QW) + pad16(4LL * nP) + 256LL * W * tiles + pad16(4LL * nR);
+    return kFrameHdrBytes + pad16(4LL * m) + pad16(8LL * m * QW) + pad16(4LL * nP) + 256LL * W * tiles +
+           twin_bytes(nP, QW) + pad16(4LL * nR);
 }
 
 __device__ __forceinline__ Frame frame_at(char *p, int m, int QW, int nP, int W)
@@ -150,6 +174,14 @@ __device__ __forceinline__ Frame frame_at(char *p, int m, int QW, int nP, int W)
     q += pad16(4LL * nP);
     f.rows = reinterpret_cast<uint64_t *>(q);
     q += 256LL * W * ((nP + 31) >> 5);
+    f.rep = nullptr;
+    f.dup = nullptr;
+    if (kPrune) {
+        f.rep = reinterpret_cast<int32_t *>(q);
+        q += pad16(4LL * nP);
+        f.dup = reinterpret_cast<uint64_t *>(q);
+        q += pad16(8LL * QW);
+    }
     f.R = reinterpret_cast<int32_t *>(q);
     return f;
 }
@@ -629,7 +661,8 @@ __device__ bool q_any_superset(const Ctx &c, const uint64_t *Q, int QW, int LW, 
 // Q' over the prefix of X: mq = OR of the columns listed in J (stride QW)
 // over the first LW words, the last cut by `last`. Eight loads per lane in
 // flight. Returns |Q'|.
-__device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp)
+__device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
+                       const uint64_t *dup)
 {
     const int lane = c.lane;
     Scratch &S = c.s;
@@ -652,6 +685,7 @@ __device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last,
             for (int k = 0; k < kUnionLoads; ++k) m |= x[k];
         }
         if (w == LW - 1) m &= last;
+        if (kPrune && v) m &= ~dup[w]; // removed candidates are in neither P nor Q
         if (v) S.mq[w] = m;
         total += __popcll(m);
     }
@@ -662,7 +696,7 @@ __device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last,
 // q_union and, fused with it, the uncompressed child columns of
 // q_copy_columns (every word loaded once, stored as it is OR-ed).
 __device__ int q_union_copy(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
-                            uint64_t *dst, int QWd)
+                            uint64_t *dst, int QWd, const uint64_t *dup)
 {
     const int lane = c.lane;
     Scratch &S = c.s;
@@ -671,7 +705,8 @@ __device__ int q_union_copy(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t 
         const int w = w0 + lane;
         const bool v = w < LW;
         const bool vd = w < QWd;
-        const uint64_t cut = w == LW - 1 ? last : ~0ULL;
+        uint64_t cut = w == LW - 1 ? last : ~0ULL;
+        if (kPrune && v) cut &= ~dup[w];
         const uint64_t *base = Q + (v ? w : 0);
         uint64_t m = 0;
         for (int t = 0; t < mp; t += kUnionLoads) {
@@ -726,7 +761,7 @@ __device__ void q_compress_masks(int lane, const uint64_t *mq, int32_t *offq, ui
 // are zero in every column of L' already. Words [LW, QWd) are zeroed for
 // the P' bits that follow.
 __device__ void q_copy_columns(int lane, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
-                               uint64_t *dst, int QWd)
+                               uint64_t *dst, int QWd, const uint64_t *dup)
 {
     // mp * QWd words: the frame fits the stack, far below 2^31 words
     const unsigned total = (unsigned)mp * (unsigned)QWd;
@@ -745,6 +780,7 @@ __device__ void q_copy_columns(int lane, const uint64_t *Q, int QW, int LW, uint
                 if (w < LW) {
                     x[u] = Q[(int64_t)J[t] * QW + w];
                     if (w == LW - 1) x[u] &= last;
+                    if (kPrune) x[u] &= ~dup[w];
                 }
             }
         }
@@ -904,6 +940,8 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const int i = F.h->i;
     __syncwarp(); // every lane has read the header before lane 0 advances the cursor
     if (lane == 0) F.h->i = i + 1;
+    // a removed candidate is never popped: no node
+    if (kPrune && F.rep[i] < i) return nullptr;
     c.nodes += 1;
 
     // Step 2: L' = L n N(x) is the row of x (lane w holds word w).
@@ -925,7 +963,16 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const uint64_t last = (lim & 63) ? ((1ULL << (lim & 63)) - 1) : ~0ULL;
     const bool rejected = lim > 0 && q_any_superset(c, F.Q, QW, LW, last, J, mp);
     if (lane == 0) tadd(a, c, 14, t_q);
-    {
+    if constexpr (kPrune) {
+        // as below, with Q = the inherited Q and the P entries popped before
+        // x (the removed ones are not); the later rows are added after the
+        // expansion has counted the ones still in P
+        int nrm = 0;
+        for (int w = lane; w < LW; w += 32) nrm += __popcll(F.dup[w] & (w == LW - 1 ? last : ~0ULL));
+        nrm = (int)__reduce_add_sync(kFull, (unsigned)nrm);
+        const uint64_t nq = (uint64_t)(nQ + i - nrm), rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
+        c.bytes += 8ULL * ((uint64_t)W + (rows < cols ? rows : cols));
+    } else {
         // algorithmic bytes: x's row, the cheaper of the Q rows and the L'
         // columns over Q (|Q| = nQ + i here), and the later P rows when maximal
         const uint64_t nq = (uint64_t)(nQ + i), rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
@@ -938,7 +985,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 
     // Step 4: maximal expansion over P positions (i, nP).
     uint64_t rsum = 0;
-    int pn = 0, nfull = 0;
+    int pn = 0, nfull = 0, nrest = 0;
     const int ntiles = (nP + 31) >> 5;
     for (int t0 = (i + 1) >> 5; t0 < ntiles; t0 += kTiles) {
         int cnt[kTiles];
@@ -946,7 +993,11 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 #pragma unroll
         for (int u = 0; u < kTiles; ++u) {
             const int k = (t0 + u) * 32 + lane;
-            const bool valid = (t0 + u < ntiles) && k > i && k < nP;
+            bool valid = (t0 + u < ntiles) && k > i && k < nP;
+            if (kPrune) {
+                valid = valid && F.rep[k] >= i; // still in P at this pop
+                nrest += __popc(__ballot_sync(kFull, valid));
+            }
             const bool full = valid && cnt[u] == mp;
             const bool part = valid && cnt[u] > 0 && cnt[u] < mp && (!kExt || cnt[u] >= a.min_l);
             const int g = (full || part) ? F.gid[k] : 0;
@@ -966,6 +1017,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         }
     }
     if (lane == 0) tadd(a, c, 1, t_scan);
+    if (kPrune) c.bytes += 8ULL * (uint64_t)W * (uint64_t)nrest;
     rsum = warp_sum64(rsum);
     const int xg = F.gid[i];
     const uint64_t Rs = F.h->Rsum + key_u(xg) + rsum;
@@ -1015,9 +1067,9 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     uint64_t *dQ = reinterpret_cast<uint64_t *>(cp + kFrameHdrBytes + pad16(4LL * mp));
     int nQd = 0;
     if (spec)
-        nQd = q_union_copy(c, F.Q, QW, LW, last, J, mp, dQ, QWcopy);
+        nQd = q_union_copy(c, F.Q, QW, LW, last, J, mp, dQ, QWcopy, F.dup);
     else if (lim > 0)
-        nQd = q_union(c, F.Q, QW, LW, last, J, mp);
+        nQd = q_union(c, F.Q, QW, LW, last, J, mp, F.dup);
     const bool compress = kCompressDen * ((nQd + 63) >> 6) <= kCompressNum * LW;
     if (lane == 0) F.h->copy_hint = compress ? 0 : 1;
     if (compress && nQd > 0) q_compress_masks(lane, S.mq, S.offq, S.cmq, LW);
@@ -1055,12 +1107,19 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     for (int k = lane; k < pn; k += 32) D.gid[k] = (int32_t)(S.pkey[k] & id_mask);
     compact_ids(c, F.Lid, J, mp, D.Lid);
     build_child_rows(c, F.rows, W, S.psrc, pn, D.rows, Wd);
+    if (kPrune) {
+        // twin classes of P' (the sort lists are free again: P' is in the frame)
+        twins::twin_keys(lane, D.rows, Wd, 0, pn, mp, S.pkey2, S.psrc2);
+        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, mp));
+        twins::twin_assign(lane, D.rows, Wd, 0, pn, mp, S.pkey2, S.psrc2, D.rep);
+        twins::set_dup(lane, D.rep, pn, qposd, D.dup, QWd);
+    }
     t_qc = tnow(a);
     if (compress) {
         zero_words(c, D.Q, (int64_t)mp * QWd);
         if (nQd > 0) q_child_columns(lane, S.mq, S.cmq, S.offq, c.sbuf, F.Q, QW, LW, J, mp, D.Q, QWd);
     } else if (!spec) {
-        q_copy_columns(lane, F.Q, QW, LW, last, J, mp, D.Q, QWd);
+        q_copy_columns(lane, F.Q, QW, LW, last, J, mp, D.Q, QWd, F.dup);
     }
     const uint64_t t_tr = tnow(a);
     rows_to_columns(lane, D.rows, Wd, nullptr, pn, mp, D.Q, QWd, qposd);
@@ -1207,7 +1266,7 @@ __device__ __forceinline__ char *take_list_out(Ctx &c, const ListOut &o)
 // universe of N2(r), the check against the earlier-ranked candidates, the
 // expansion by the later-ranked ones, and the level-1 frame at the bottom
 // of the stack. Returns true when a frame was pushed.
-constexpr bool kLists = MBE_LIST_PATH != 0;
+constexpr bool kLists = MBE_LIST_PATH != 0 && MBE_PRUNE == 0;
 
 __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r, int graph, int part, int parts)
 {
@@ -1215,8 +1274,14 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     const uint64_t t_root = tnow(a);
     const int ro = G.u_off[r];
     const int d = G.u_off[r + 1] - ro;
-    // never popped: an isolated vertex, or one of degree below the size filter
+    // never popped: an isolated vertex, one of degree below the size filter,
+    // or (pruned variant) one with the neighbourhood of a smaller id: the
+    // top-level L is V, so its twin class shares its degree and the smallest
+    // id of the class is popped first
     if (d == 0 || (kExt && d < a.min_l)) return false;
+    // (twin classes of this graph: local ids, indexed from its u_off base)
+    const int32_t *trep = kPrune ? a.trep + a.graphs[graph].u_off_base : nullptr;
+    if (kPrune && trep[r] < r) return false;
     // a pre-split root: every part rebuilds the root node, part 0 alone
     // counts it, and part p pops its own contiguous share of P'
     const bool first = part == 0;
@@ -1358,14 +1423,17 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         // earlier-ranked candidates were popped before r (those below the size
         // filter never are); cnt > 0 for every discovered candidate
         const bool earlier = du < d || (du == d && u < r);
-        bool ql = valid && earlier && (!kExt || du >= a.min_l);
+        // pruned: a later candidate left P at its twin's pop if that came
+        // before r's; an earlier one that was removed never joined Q
+        const bool removed = kPrune && valid && (earlier ? trep[u] < u : (du == d && trep[u] < r));
+        bool ql = valid && !removed && earlier && (!kExt || du >= a.min_l);
         if (__ballot_sync(kFull, ql && cnt == d)) { // r's node is not maximal
             if (lane == 0) tadd(a, c, 0, t_root);
             return false;
         }
-        bool full = valid && !earlier && cnt == d;
+        bool full = valid && !removed && !earlier && cnt == d;
         bool qpart = ql;
-        bool ppart = valid && !earlier && cnt < d && (!kExt || cnt >= a.min_l);
+        bool ppart = valid && !removed && !earlier && cnt < d && (!kExt || cnt >= a.min_l);
         if (full) rsum += key_u(u);
         if (a.emit || (kExt && a.min_r > 1)) {
             unsigned fb = __ballot_sync(kFull, full);
@@ -1443,6 +1511,13 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     zero_words(c, D.Q, (int64_t)d * QW);
     if (qn > 0) rows_to_columns(lane, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
     rows_to_columns(lane, D.rows, W, nullptr, pn, d, D.Q, QW, qn);
+    if (kPrune) {
+        // twin classes of P' (the sort lists are free again: P' is in the frame)
+        twins::twin_keys(lane, D.rows, W, 0, pn, d, S.pkey2, S.psrc2);
+        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, d));
+        twins::twin_assign(lane, D.rows, W, 0, pn, d, S.pkey2, S.psrc2, D.rep);
+        twins::set_dup(lane, D.rep, pn, qn, D.dup, QW);
+    }
     if (a.emit)
         for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {
@@ -1870,9 +1945,9 @@ __global__ void __launch_bounds__(256, MBE_SEARCH_MIN_BLOCKS) MBE_SEARCH_KERNEL(
 
 } // namespace
 
-#if MBE_LIST_PATH
+#if MBE_LIST_PATH || MBE_PRUNE
 
-int search_lists_fit_shape(int threads, int blocks_per_sm_req)
+int MBE_VARIANT_FIT(int threads, int blocks_per_sm_req)
 {
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, MBE_SEARCH_KERNEL) != cudaSuccess) return 0;
@@ -1884,7 +1959,7 @@ int search_lists_fit_shape(int threads, int blocks_per_sm_req)
     return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
 }
 
-cudaError_t launch_search_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
+cudaError_t MBE_VARIANT_LAUNCH(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
 {
     static int smem_set[64] = {0};
     int dev = 0;
@@ -1915,15 +1990,19 @@ int search_fit_shape(int threads, int blocks_per_sm_req)
     cudaFuncSetAttribute(search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 32 * search_smem_per_warp());
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel, threads, smem) != cudaSuccess) return 0;
-    // the list variant must fit the same shape
+    // the list and pruned variants must fit the same shape
     const int per_sm_l = search_lists_fit_shape(threads, per_sm);
     if (per_sm_l <= 0) return per_sm_l;
     if (per_sm_l < per_sm) per_sm = per_sm_l;
+    const int per_sm_p = search_prune_fit_shape(threads, per_sm);
+    if (per_sm_p <= 0) return per_sm_p;
+    if (per_sm_p < per_sm) per_sm = per_sm_p;
     return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
 }
 
 cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
 {
+    if (a.prune) return launch_search_prune(a, blocks, threads, stream);
     if (a.lists) return launch_search_lists(a, blocks, threads, stream);
     // the dynamic shared memory limit is raised once to the largest block
     // (no attribute calls between captured launches)

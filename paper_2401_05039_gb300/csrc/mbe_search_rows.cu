@@ -34,15 +34,26 @@
 #include "mbe_bits.h"
 #include "mbe_emit.cuh"
 #include "mbe_internal.h"
+#include "mbe_twins.cuh"
 
 // MBE_LIST_PATH = 1 builds the variant with the sorted-list path for level
 // sets wider than the bitset limit (mbe_search_rows_lists.cu); it is launched
-// only for graphs with such roots.
+// only for graphs with such roots. MBE_PRUNE = 1 builds the pruned variant
+// (mbe_search_rows_prune.cu: iMBE's L - L' removal, bitset level sets only).
 #ifndef MBE_LIST_PATH
 #define MBE_LIST_PATH 0
 #endif
-#if MBE_LIST_PATH
+#ifndef MBE_PRUNE
+#define MBE_PRUNE 0
+#endif
+#if MBE_PRUNE
+#define MBE_ROWS_KERNEL search_rows_prune_kernel
+#define MBE_VARIANT_FIT search_rows_prune_fit_shape
+#define MBE_VARIANT_LAUNCH launch_search_rows_prune
+#elif MBE_LIST_PATH
 #define MBE_ROWS_KERNEL search_rows_lists_kernel
+#define MBE_VARIANT_FIT search_rows_lists_fit_shape
+#define MBE_VARIANT_LAUNCH launch_search_rows_lists
 #else
 #define MBE_ROWS_KERNEL search_rows_kernel
 #endif
@@ -50,8 +61,11 @@
 namespace mbe {
 namespace {
 
-// The extended variant (MBE_LIST_PATH = 1) also carries the size filter.
-constexpr bool kExt = MBE_LIST_PATH != 0;
+// The extended variants (list path, pruning) also carry the size filter.
+constexpr bool kExt = MBE_LIST_PATH != 0 || MBE_PRUNE != 0;
+// The pruned variant: every frame carries, per P entry, the first position
+// of its twin class (twins::twin_reps) and a removal mask over P.
+constexpr bool kPrune = MBE_PRUNE != 0;
 
 constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
@@ -104,16 +118,24 @@ struct Frame {
     int32_t *Lid;    // [m] vertex ids of L (V side)
     int32_t *gid;    // [n] candidate ids (U side)
     uint64_t *rows;  // [ceil(n/32)][W][32]
+    int32_t *rep;    // pruned variant: [nP] first P position with the same row (twins::twin_reps)
+    uint64_t *dup;   // pruned variant: [ceil(nP/64)] bit j set when rep[j] < j
     int32_t *R;      // [nR]
 };
 
-__device__ __forceinline__ int64_t frame_bytes(int m, int n, int W, int nR)
+// Bytes of the pruned variant's twin sections (none in the other variants).
+__device__ __forceinline__ int64_t twin_bytes(int nP)
 {
-    int64_t tiles = (n + 31) >> 5;
-    return 64 + pad16(4LL * m) + pad16(4LL * n) + 256LL * W * tiles + pad16(4LL * nR);
+    return kPrune ? pad16(4LL * nP) + pad16(8LL * ((nP + 63) >> 6)) : 0;
 }
 
-__device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W)
+__device__ __forceinline__ int64_t frame_bytes(int m, int n, int W, int nR, int nP)
+{
+    int64_t tiles = (n + 31) >> 5;
+    return 64 + pad16(4LL * m) + pad16(4LL * n) + 256LL * W * tiles + twin_bytes(nP) + pad16(4LL * nR);
+}
+
+__device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W, int nP)
 {
     Frame f;
     f.h = reinterpret_cast<FrameHdr *>(p);
@@ -124,6 +146,14 @@ __device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W)
     q += pad16(4LL * n);
     f.rows = reinterpret_cast<uint64_t *>(q);
     q += 256LL * W * ((n + 31) >> 5);
+    f.rep = nullptr;
+    f.dup = nullptr;
+    if (kPrune) {
+        f.rep = reinterpret_cast<int32_t *>(q);
+        q += pad16(4LL * nP);
+        f.dup = reinterpret_cast<uint64_t *>(q);
+        q += pad16(8LL * ((nP + 63) >> 6));
+    }
     f.R = reinterpret_cast<int32_t *>(q);
     return f;
 }
@@ -131,7 +161,7 @@ __device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W)
 __device__ __forceinline__ Frame frame_of(char *p)
 {
     const FrameHdr *h = reinterpret_cast<const FrameHdr *>(p);
-    return frame_at(p, h->m, h->nQ + h->nP, h->W);
+    return frame_at(p, h->m, h->nQ + h->nP, h->W, h->nP);
 }
 
 __device__ __forceinline__ int64_t row_word(int k, int w, int W)
@@ -520,6 +550,8 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const int kx = nQ + i;
     __syncwarp(); // every lane has read the header before lane 0 advances the cursor
     if (lane == 0) F.h->i = i + 1;
+    // a removed candidate is never popped: no node
+    if (kPrune && F.rep[i] < i) return nullptr;
     c.nodes += 1;
 
     // Step 2: L' = L n N(x) is the row of x (lane w holds word w).
@@ -544,13 +576,25 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
                 rejected = true;
                 break;
             }
-            const bool part = valid && cnt[u] > 0;
+            // removed candidates (P positions before x with an earlier twin)
+            // are in neither P nor Q
+            const bool part = valid && cnt[u] > 0 && !(kPrune && k >= nQ && F.rep[k - nQ] < k - nQ);
             const unsigned bal = __ballot_sync(kFull, part);
             if (part) S.qsrc[qn + __popc(bal & lanemask_lt())] = k;
             qn += __popc(bal);
         }
     }
-    {
+    if constexpr (kPrune) {
+        // as below, with Q = the inherited Q and the P entries popped before
+        // x (the removed ones are not); the later rows are added after the
+        // expansion has counted the ones still in P
+        int nrm = 0;
+        for (int w = lane; w < ((i + 63) >> 6); w += 32)
+            nrm += __popcll(F.dup[w] & ((w + 1) * 64 <= i ? ~0ULL : ((1ULL << (i & 63)) - 1)));
+        nrm = (int)__reduce_add_sync(kFull, (unsigned)nrm);
+        const uint64_t nq = (uint64_t)(kx - nrm), rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
+        c.bytes += 8ULL * ((uint64_t)W + (rows < cols ? rows : cols));
+    } else {
         // algorithmic bytes: x's row, the cheaper of the Q rows and the L'
         // columns over Q (|Q| = kx here), and the later P rows when maximal
         const uint64_t nq = (uint64_t)kx, rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
@@ -563,7 +607,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 
     // Step 4: maximal expansion over positions (kx, n).
     uint64_t rsum = 0;
-    int pn = 0, nfull = 0;
+    int pn = 0, nfull = 0, nrest = 0;
     const int ntiles = (n + 31) >> 5;
     for (int t0 = (kx + 1) >> 5; t0 < ntiles; t0 += kTiles) {
         int cnt[kTiles];
@@ -571,7 +615,11 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
 #pragma unroll
         for (int u = 0; u < kTiles; ++u) {
             const int k = (t0 + u) * 32 + lane;
-            const bool valid = (t0 + u < ntiles) && k > kx && k < n;
+            bool valid = (t0 + u < ntiles) && k > kx && k < n;
+            if (kPrune) {
+                valid = valid && F.rep[k - nQ] >= i; // still in P at this pop
+                nrest += __popc(__ballot_sync(kFull, valid));
+            }
             const bool full = valid && cnt[u] == mp;
             const bool part = valid && cnt[u] > 0 && cnt[u] < mp && (!kExt || cnt[u] >= a.min_l);
             const int g = (full || part) ? F.gid[k] : 0;
@@ -591,6 +639,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         }
     }
     if (lane == 0) tadd(a, c, 1, t_scan);
+    if (kPrune) c.bytes += 8ULL * (uint64_t)W * (uint64_t)nrest;
     rsum = warp_sum64(rsum);
     const int xg = F.gid[kx];
     const uint64_t Rs = F.h->Rsum + key_u(xg) + rsum;
@@ -623,7 +672,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const int Wd = (mp + 63) >> 6;
     const int nd = qn + pn;
     const int nRd = a.emit ? F.h->nR + 1 + nfull : 0;
-    const int64_t sz = frame_bytes(mp, nd, Wd, nRd);
+    const int64_t sz = frame_bytes(mp, nd, Wd, nRd, pn);
     char *cp = fp + F.h->bytes;
     if (cp + sz > c.limit) {
         if (lane == 0) set_error(a, kErrArena);
@@ -633,11 +682,18 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     int key_bits = a.key_shift + (32 - __clz(mp));
     warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, pn, key_bits);
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
-    Frame D = frame_at(cp, mp, nd, Wd);
+    Frame D = frame_at(cp, mp, nd, Wd, pn);
     for (int k = lane; k < qn; k += 32) D.gid[k] = F.gid[S.qsrc[k]];
     for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
     compact_ids(c, F.Lid, Lw, W, D.Lid);
     build_child_rows(c, F.rows, W, S.qsrc, qn, S.psrc, pn, D.rows, Wd);
+    if (kPrune) {
+        // twin classes of P' (the sort lists are free again: P' is in the frame)
+        twins::twin_keys(lane, D.rows, Wd, qn, pn, mp, S.pkey2, S.psrc2);
+        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, mp));
+        twins::twin_assign(lane, D.rows, Wd, qn, pn, mp, S.pkey2, S.psrc2, D.rep);
+        twins::set_dup(lane, D.rep, pn, 0, D.dup, (pn + 63) >> 6);
+    }
     if (a.emit) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
     if (lane == 0) {
         FrameHdr h;
@@ -676,13 +732,13 @@ __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv
     const int W = (mp + 63) >> 6, n = nQd + pn;
     const int64_t tiles = (n + 31) >> 5;
     const int nRd = a.emit ? na + nb : 0;
-    const int64_t sz = frame_bytes(mp, n, W, nRd);
+    const int64_t sz = frame_bytes(mp, n, W, nRd, pn);
     if (n > e.ncap || ((uintptr_t)cp & 15) || cp + sz > e.limit) {
         if (lane == 0) set_error(a, kErrArena);
         return nullptr;
     }
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
-    Frame D = frame_at(cp, mp, n, W);
+    Frame D = frame_at(cp, mp, n, W, pn);
     for (int k = lane; k < n; k += 32) {
         const int u = k < nQd ? Qg[k] : (int32_t)(Pk[k - nQd] & id_mask);
         e.mark[u] = k;
@@ -751,7 +807,7 @@ __device__ __forceinline__ char *take_list_out(Ctx &c, const ListOut &o)
     return o.child;
 }
 
-constexpr bool kLists = MBE_LIST_PATH != 0;
+constexpr bool kLists = MBE_LIST_PATH != 0 && MBE_PRUNE == 0;
 
 // ------------------------------------------------------------- root task
 // The top-level iteration for candidate r: L' = N(r), the root-local
@@ -766,6 +822,12 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     const int d = G.u_off[r + 1] - ro;
     // never popped: an isolated vertex, or one of degree below the size filter
     if (d == 0 || (kExt && d < a.min_l)) return false;
+    // pruned variant: a vertex with the neighbourhood of a smaller id is
+    // never popped (the top-level L is V: twins share the degree, and the
+    // smallest id of the class comes first)
+    // (twin classes of this graph: local ids, indexed from its u_off base)
+    const int32_t *trep = kPrune ? a.trep + a.graphs[graph].u_off_base : nullptr;
+    if (kPrune && trep[r] < r) return false;
     // a pre-split root: every part rebuilds the root node, part 0 alone
     // counts it, and part p pops its own contiguous share of P'
     const bool first = part == 0;
@@ -879,14 +941,17 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         // earlier-ranked candidates were popped before r (those below the size
         // filter never are); cnt > 0 for every discovered candidate
         const bool earlier = du < d || (du == d && u < r);
-        bool ql = valid && earlier && (!kExt || du >= a.min_l);
+        // pruned: a later candidate left P at its twin's pop if that came
+        // before r's; an earlier one that was removed never joined Q
+        const bool removed = kPrune && valid && (earlier ? trep[u] < u : (du == d && trep[u] < r));
+        bool ql = valid && !removed && earlier && (!kExt || du >= a.min_l);
         if (__ballot_sync(kFull, ql && cnt == d)) { // r's node is not maximal
             if (lane == 0) tadd(a, c, 0, t_root);
             return false;
         }
-        bool full = valid && !earlier && cnt == d;
+        bool full = valid && !removed && !earlier && cnt == d;
         bool qpart = ql;
-        bool ppart = valid && !earlier && cnt < d && (!kExt || cnt >= a.min_l);
+        bool ppart = valid && !removed && !earlier && cnt < d && (!kExt || cnt >= a.min_l);
         if (full) rsum += key_u(u);
         if (a.emit || (kExt && a.min_r > 1)) {
             unsigned fb = __ballot_sync(kFull, full);
@@ -945,7 +1010,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
 
     const int nd = qn + pn;
     const int nRd = a.emit ? 1 + nfull : 0;
-    const int64_t sz = frame_bytes(d, nd, W, nRd);
+    const int64_t sz = frame_bytes(d, nd, W, nRd, pn);
     char *cp = c.arena;
     if (cp + sz > c.limit) {
         if (lane == 0) set_error(a, kErrArena);
@@ -955,11 +1020,18 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     int key_bits = a.key_shift + (32 - __clz(d));
     warp_sort(c, S.pkey, S.psrc, S.pkey2, S.psrc2, pn, key_bits);
     const uint64_t id_mask = (1ULL << a.key_shift) - 1;
-    Frame D = frame_at(cp, d, nd, W);
+    Frame D = frame_at(cp, d, nd, W, pn);
     for (int k = lane; k < qn; k += 32) D.gid[k] = S.ugid[S.qsrc[k]];
     for (int k = lane; k < pn; k += 32) D.gid[qn + k] = (int32_t)(S.pkey[k] & id_mask);
     for (int k = lane; k < d; k += 32) D.Lid[k] = G.u_adj[ro + k];
     build_child_rows(c, S.urows, W, S.qsrc, qn, S.psrc, pn, D.rows, W);
+    if (kPrune) {
+        // twin classes of P' (the sort lists are free again: P' is in the frame)
+        twins::twin_keys(lane, D.rows, W, qn, pn, d, S.pkey2, S.psrc2);
+        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, d));
+        twins::twin_assign(lane, D.rows, W, qn, pn, d, S.pkey2, S.psrc2, D.rep);
+        twins::set_dup(lane, D.rep, pn, 0, D.dup, (pn + 63) >> 6);
+    }
     if (a.emit)
         for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {
@@ -1352,9 +1424,9 @@ __global__ void __launch_bounds__(256, 2) MBE_ROWS_KERNEL(SearchArgs a)
 
 } // namespace
 
-#if MBE_LIST_PATH
+#if MBE_LIST_PATH || MBE_PRUNE
 
-int search_rows_lists_fit_shape(int threads, int blocks_per_sm_req)
+int MBE_VARIANT_FIT(int threads, int blocks_per_sm_req)
 {
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, MBE_ROWS_KERNEL) != cudaSuccess) return 0;
@@ -1366,7 +1438,7 @@ int search_rows_lists_fit_shape(int threads, int blocks_per_sm_req)
     return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
 }
 
-cudaError_t launch_search_rows_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
+cudaError_t MBE_VARIANT_LAUNCH(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
 {
     static int smem_set[64] = {0};
     int dev = 0;
@@ -1399,15 +1471,19 @@ int search_rows_fit_shape(int threads, int blocks_per_sm_req)
     int per_sm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_rows_kernel, threads, smem) != cudaSuccess)
         return 0;
-    // the list variant must fit the same shape
+    // the list and pruned variants must fit the same shape
     const int per_sm_l = search_rows_lists_fit_shape(threads, per_sm);
     if (per_sm_l <= 0) return per_sm_l;
     if (per_sm_l < per_sm) per_sm = per_sm_l;
+    const int per_sm_p = search_rows_prune_fit_shape(threads, per_sm);
+    if (per_sm_p <= 0) return per_sm_p;
+    if (per_sm_p < per_sm) per_sm = per_sm_p;
     return blocks_per_sm_req < per_sm ? blocks_per_sm_req : per_sm;
 }
 
 cudaError_t launch_search_rows(const SearchArgs &a, int blocks, int threads, cudaStream_t stream)
 {
+    if (a.prune) return launch_search_rows_prune(a, blocks, threads, stream);
     if (a.lists) return launch_search_rows_lists(a, blocks, threads, stream);
     // the dynamic shared memory limit is raised once to the largest block
     // (no attribute calls between captured launches)

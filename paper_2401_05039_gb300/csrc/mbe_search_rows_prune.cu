@@ -1,0 +1,5 @@
+// The row-layout search kernel with iMBE's L - L' removal (Section II-C,
+// embedded pruning): the same source as mbe_search_rows.cu, compiled as its
+// own translation unit (bitset level sets only).
+#define MBE_PRUNE 1
+#include "mbe_search_rows.cu"

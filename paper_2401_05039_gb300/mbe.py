@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
                 ("root_end", ctypes.c_int32), ("arena_bytes", ctypes.c_int64), ("model", ctypes.c_void_p),
                 ("per_root", ctypes.c_void_p), ("exec_order", ctypes.c_void_p), ("n_exec", ctypes.c_int32),
                 ("class_params", ctypes.c_void_p), ("layout", ctypes.c_int32), ("min_r", ctypes.c_int32),
-                ("min_l", ctypes.c_int32)]
+                ("min_l", ctypes.c_int32), ("prune", ctypes.c_int32)]
 
 
 class ClassParams(ctypes.Structure):

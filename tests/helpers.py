@@ -76,3 +76,13 @@ def is_closed_pair(g, R, L, adj=None):
 
 def canon(pairs):
     return sorted((tuple(sorted(r)), tuple(sorted(l))) for r, l in pairs)
+
+
+def twin_graph(rng, nU, nV, n_base, p, flip):
+    """Each U vertex copies one of n_base random rows of density p and flips
+    every bit with probability flip: many vertices share a neighbourhood,
+    in G and (far more often) inside the level sets of a search."""
+    base = rng.random((n_base, nV)) < p
+    rows = base[rng.integers(0, n_base, size=nU)] ^ (rng.random((nU, nV)) < flip)
+    us, vs = np.nonzero(rows)
+    return graph(nU, nV, zip(us.tolist(), vs.tolist()), f"twins{nU}x{nV}")

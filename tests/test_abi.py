@@ -61,6 +61,7 @@ int main(void) {{
   printf("%zu %zu %zu %zu %zu\\n", offsetof(mbe_options, layout), sizeof(mbe_class_params),
          offsetof(mbe_class_params, layout), offsetof(mbe_class_params, tuned_ms),
          offsetof(mbe_class_params, default_ms));
+  printf("%zu\\n", offsetof(mbe_options, prune));
   return 0;
 }}''')
     exe = tmp_path / "layout"
@@ -73,6 +74,7 @@ int main(void) {{
     assert vals[8:11] == [R.device_ms.offset, R.status.offset, R.n_donations.offset]
     C = m.ClassParams
     assert vals[11:16] == [O.layout.offset, ctypes.sizeof(C), C.layout.offset, C.tuned_ms.offset, C.default_ms.offset]
+    assert vals[16] == O.prune.offset
 
 
 def test_compress_helper_matches_bit_gather(tmp_path):
