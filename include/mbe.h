@@ -98,7 +98,8 @@ int mbe_graph_info(const mbe_graph *g, int32_t *nU, int32_t *nV, int64_t *nE, in
  * [24] forming Q', [25] copying or compressing the parent's columns, [26]
  * transposing P'; [27] child builds that copied the columns uncompressed;
  * both layouts: [28] ns from the launch to the end of the worker's last
- * task, [29] ns the worker spent idle between tasks (before that end).
+ * task, [29] ns the worker spent idle between tasks (before that end), [30]
+ * (pruned variants) ns finding the twin classes of new frames.
  * The timers read the global timer and slow the search. This copies up to
  * max_workers of them (MBE_TRACE_WORDS uint64 each) to `host` and
  * returns how many were copied. MBE_DEADLINE_MS bounds any single launch

@@ -142,15 +142,19 @@ struct Frame {
     uint64_t *Q;     // [m][QW] columns over X = Q then P (nQ + nP positions)
     int32_t *gid;    // [nP] P candidate ids (U side)
     uint64_t *rows;  // [ceil(nP/32)][W][32] P rows
-    int32_t *rep;    // pruned variant: [nP] first P position with the same row (see twin_reps)
-    uint64_t *dup;   // pruned variant: [QW] bit qpos + j set when rep[j] < j
+    int32_t *rep;    // pruned variant: [nP] first P position with the same row (mbe_twins.cuh)
+    int32_t *pre;    // pruned variant: [nP] removed P positions before j (rep[k] < k, k < j)
     int32_t *R;      // [nR]
 };
 
 // Bytes of the pruned variant's twin sections (none in the other variants).
+// A removed P position needs no mask of its own: its bits are left out of
+// the frame's columns, which are only read over the prefix of popped
+// positions, so it is in no Q' (its row, still in the frame, lets it join
+// R' at its representative's pop).
 __device__ __forceinline__ int64_t twin_bytes(int nP, int QW)
 {
-    return kPrune ? pad16(4LL * nP) + pad16(8LL * QW) : 0;
+    return kPrune ? 2 * pad16(4LL * nP) : 0;
 }
 
 __device__ __forceinline__ int64_t frame_bytes(int m, int QW, int nP, int W, int nR)
@@ -175,12 +179,12 @@ __device__ __forceinline__ Frame frame_at(char *p, int m, int QW, int nP, int W)
     f.rows = reinterpret_cast<uint64_t *>(q);
     q += 256LL * W * ((nP + 31) >> 5);
     f.rep = nullptr;
-    f.dup = nullptr;
+    f.pre = nullptr;
     if (kPrune) {
         f.rep = reinterpret_cast<int32_t *>(q);
         q += pad16(4LL * nP);
-        f.dup = reinterpret_cast<uint64_t *>(q);
-        q += pad16(8LL * QW);
+        f.pre = reinterpret_cast<int32_t *>(q);
+        q += pad16(4LL * nP);
     }
     f.R = reinterpret_cast<int32_t *>(q);
     return f;
@@ -396,6 +400,29 @@ __device__ __forceinline__ void warp_sort(Ctx &c, uint64_t *k0, int32_t *v0, uin
                                           int key_bits)
 {
     warp_sort_impl(c.lane, c.hist, k0, v0, k1, v1, n, key_bits);
+}
+
+// Pruned variant: the twin sections (rep, pre) of a new frame whose n P
+// rows (W words, m bits) are in place. Frames of at most 32 P rows take one
+// warp match; larger ones (or a digest collision) one sort of (digest,
+// position) keys. The sort lists are free again here (P' is in the frame).
+// Out of line: it runs once per frame, and inlined it crowds the node
+// loop out of the instruction cache (measured: Chung-Lu 20k 184 -> 160 ms).
+__device__ __noinline__ void twin_sections(int lane, uint32_t *hist, const uint64_t *rows, int32_t *rep, int32_t *pre,
+                                           uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v1, int W, int off, int n,
+                                           int m)
+{
+    if (n <= 32 && twins::twin_small(lane, rows, W, off, n, rep, pre)) return;
+    twins::twin_keys(lane, rows, W, off, n, m, k0, v0);
+    warp_sort_impl(lane, hist, k0, v0, k1, v1, n, twins::twin_key_bits(n, m));
+    twins::twin_assign(lane, rows, W, off, n, m, k0, v0, rep);
+    twins::set_pre(lane, rep, n, pre);
+}
+
+__device__ __forceinline__ void frame_twins(int lane, uint32_t *hist, const Scratch &S, const Frame &D, int W, int n,
+                                            int m)
+{
+    twin_sections(lane, hist, D.rows, D.rep, D.pre, S.pkey2, S.psrc2, S.pkey, S.psrc, W, 0, n, m);
 }
 
 // ---------------------------------------------------------------- row scans
@@ -661,8 +688,7 @@ __device__ bool q_any_superset(const Ctx &c, const uint64_t *Q, int QW, int LW, 
 // Q' over the prefix of X: mq = OR of the columns listed in J (stride QW)
 // over the first LW words, the last cut by `last`. Eight loads per lane in
 // flight. Returns |Q'|.
-__device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
-                       const uint64_t *dup)
+__device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp)
 {
     const int lane = c.lane;
     Scratch &S = c.s;
@@ -685,7 +711,6 @@ __device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last,
             for (int k = 0; k < kUnionLoads; ++k) m |= x[k];
         }
         if (w == LW - 1) m &= last;
-        if (kPrune && v) m &= ~dup[w]; // removed candidates are in neither P nor Q
         if (v) S.mq[w] = m;
         total += __popcll(m);
     }
@@ -696,7 +721,7 @@ __device__ int q_union(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last,
 // q_union and, fused with it, the uncompressed child columns of
 // q_copy_columns (every word loaded once, stored as it is OR-ed).
 __device__ int q_union_copy(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
-                            uint64_t *dst, int QWd, const uint64_t *dup)
+                            uint64_t *dst, int QWd)
 {
     const int lane = c.lane;
     Scratch &S = c.s;
@@ -705,8 +730,7 @@ __device__ int q_union_copy(Ctx &c, const uint64_t *Q, int QW, int LW, uint64_t 
         const int w = w0 + lane;
         const bool v = w < LW;
         const bool vd = w < QWd;
-        uint64_t cut = w == LW - 1 ? last : ~0ULL;
-        if (kPrune && v) cut &= ~dup[w];
+        const uint64_t cut = w == LW - 1 ? last : ~0ULL;
         const uint64_t *base = Q + (v ? w : 0);
         uint64_t m = 0;
         for (int t = 0; t < mp; t += kUnionLoads) {
@@ -761,7 +785,7 @@ __device__ void q_compress_masks(int lane, const uint64_t *mq, int32_t *offq, ui
 // are zero in every column of L' already. Words [LW, QWd) are zeroed for
 // the P' bits that follow.
 __device__ void q_copy_columns(int lane, const uint64_t *Q, int QW, int LW, uint64_t last, const int32_t *J, int mp,
-                               uint64_t *dst, int QWd, const uint64_t *dup)
+                               uint64_t *dst, int QWd)
 {
     // mp * QWd words: the frame fits the stack, far below 2^31 words
     const unsigned total = (unsigned)mp * (unsigned)QWd;
@@ -780,7 +804,6 @@ __device__ void q_copy_columns(int lane, const uint64_t *Q, int QW, int LW, uint
                 if (w < LW) {
                     x[u] = Q[(int64_t)J[t] * QW + w];
                     if (w == LW - 1) x[u] &= last;
-                    if (kPrune) x[u] &= ~dup[w];
                 }
             }
         }
@@ -898,13 +921,14 @@ __device__ __forceinline__ void or_bits32(uint64_t *col, int p, uint32_t v)
 // Transposes n rows (tile layout, Wr words, row k taken from position
 // pos[k] or k) into ncols column bitsets of QWd words, writing the rows as
 // bits bit0 .. bit0+n-1 of every column (OR into zeroed columns). Each
-// 32-row x 64-column block is two warp transposes.
+// 32-row x 64-column block is two warp transposes. rep (pruned variant, or
+// nullptr): row k is left out when rep[k] < k.
 __device__ void rows_to_columns(int lane, const uint64_t *rows, int Wr, const int32_t *pos, int n, int ncols,
-                                uint64_t *cols, int QWd, int bit0)
+                                uint64_t *cols, int QWd, int bit0, const int32_t *rep = nullptr)
 {
     for (int t0 = 0; t0 < n; t0 += 32) {
         const int k = t0 + lane;
-        const bool valid = k < n;
+        const bool valid = k < n && !(kPrune && rep && rep[k] < k);
         const int src = valid ? (pos ? pos[k] : k) : 0;
         const uint64_t *r = rows + row_word(src, 0, Wr);
         const int p = bit0 + t0;
@@ -967,9 +991,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         // as below, with Q = the inherited Q and the P entries popped before
         // x (the removed ones are not); the later rows are added after the
         // expansion has counted the ones still in P
-        int nrm = 0;
-        for (int w = lane; w < LW; w += 32) nrm += __popcll(F.dup[w] & (w == LW - 1 ? last : ~0ULL));
-        nrm = (int)__reduce_add_sync(kFull, (unsigned)nrm);
+        const int nrm = F.pre[i];
         const uint64_t nq = (uint64_t)(nQ + i - nrm), rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
         c.bytes += 8ULL * ((uint64_t)W + (rows < cols ? rows : cols));
     } else {
@@ -1067,9 +1089,9 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     uint64_t *dQ = reinterpret_cast<uint64_t *>(cp + kFrameHdrBytes + pad16(4LL * mp));
     int nQd = 0;
     if (spec)
-        nQd = q_union_copy(c, F.Q, QW, LW, last, J, mp, dQ, QWcopy, F.dup);
+        nQd = q_union_copy(c, F.Q, QW, LW, last, J, mp, dQ, QWcopy);
     else if (lim > 0)
-        nQd = q_union(c, F.Q, QW, LW, last, J, mp, F.dup);
+        nQd = q_union(c, F.Q, QW, LW, last, J, mp);
     const bool compress = kCompressDen * ((nQd + 63) >> 6) <= kCompressNum * LW;
     if (lane == 0) F.h->copy_hint = compress ? 0 : 1;
     if (compress && nQd > 0) q_compress_masks(lane, S.mq, S.offq, S.cmq, LW);
@@ -1108,21 +1130,19 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     compact_ids(c, F.Lid, J, mp, D.Lid);
     build_child_rows(c, F.rows, W, S.psrc, pn, D.rows, Wd);
     if (kPrune) {
-        // twin classes of P' (the sort lists are free again: P' is in the frame)
-        twins::twin_keys(lane, D.rows, Wd, 0, pn, mp, S.pkey2, S.psrc2);
-        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, mp));
-        twins::twin_assign(lane, D.rows, Wd, 0, pn, mp, S.pkey2, S.psrc2, D.rep);
-        twins::set_dup(lane, D.rep, pn, qposd, D.dup, QWd);
+        const uint64_t t_tw = tnow(a);
+        frame_twins(lane, c.hist, S, D, Wd, pn, mp);
+        if (lane == 0) tadd(a, c, 22, t_tw);
     }
     t_qc = tnow(a);
     if (compress) {
         zero_words(c, D.Q, (int64_t)mp * QWd);
         if (nQd > 0) q_child_columns(lane, S.mq, S.cmq, S.offq, c.sbuf, F.Q, QW, LW, J, mp, D.Q, QWd);
     } else if (!spec) {
-        q_copy_columns(lane, F.Q, QW, LW, last, J, mp, D.Q, QWd, F.dup);
+        q_copy_columns(lane, F.Q, QW, LW, last, J, mp, D.Q, QWd);
     }
     const uint64_t t_tr = tnow(a);
-    rows_to_columns(lane, D.rows, Wd, nullptr, pn, mp, D.Q, QWd, qposd);
+    rows_to_columns(lane, D.rows, Wd, nullptr, pn, mp, D.Q, QWd, qposd, D.rep);
     if (lane == 0 && c.dbg) {
         const uint64_t now = globaltimer();
         c.dbg[23] += now - t_qc;
@@ -1510,14 +1530,12 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     // into one column per vertex of N(r)
     zero_words(c, D.Q, (int64_t)d * QW);
     if (qn > 0) rows_to_columns(lane, S.urows, W, S.qsrc, qn, d, D.Q, QW, 0);
-    rows_to_columns(lane, D.rows, W, nullptr, pn, d, D.Q, QW, qn);
     if (kPrune) {
-        // twin classes of P' (the sort lists are free again: P' is in the frame)
-        twins::twin_keys(lane, D.rows, W, 0, pn, d, S.pkey2, S.psrc2);
-        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, d));
-        twins::twin_assign(lane, D.rows, W, 0, pn, d, S.pkey2, S.psrc2, D.rep);
-        twins::set_dup(lane, D.rep, pn, qn, D.dup, QW);
+        const uint64_t t_tw = tnow(a);
+        frame_twins(lane, c.hist, S, D, W, pn, d);
+        if (lane == 0) tadd(a, c, 22, t_tw);
     }
+    rows_to_columns(lane, D.rows, W, nullptr, pn, d, D.Q, QW, qn, D.rep);
     if (a.emit)
         for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {

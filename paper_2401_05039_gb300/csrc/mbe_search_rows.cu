@@ -118,15 +118,15 @@ struct Frame {
     int32_t *Lid;    // [m] vertex ids of L (V side)
     int32_t *gid;    // [n] candidate ids (U side)
     uint64_t *rows;  // [ceil(n/32)][W][32]
-    int32_t *rep;    // pruned variant: [nP] first P position with the same row (twins::twin_reps)
-    uint64_t *dup;   // pruned variant: [ceil(nP/64)] bit j set when rep[j] < j
+    int32_t *rep;    // pruned variant: [nP] first P position with the same row (mbe_twins.cuh)
+    int32_t *pre;    // pruned variant: [nP] removed P positions before j (rep[k] < k, k < j)
     int32_t *R;      // [nR]
 };
 
 // Bytes of the pruned variant's twin sections (none in the other variants).
 __device__ __forceinline__ int64_t twin_bytes(int nP)
 {
-    return kPrune ? pad16(4LL * nP) + pad16(8LL * ((nP + 63) >> 6)) : 0;
+    return kPrune ? 2 * pad16(4LL * nP) : 0;
 }
 
 __device__ __forceinline__ int64_t frame_bytes(int m, int n, int W, int nR, int nP)
@@ -147,12 +147,12 @@ __device__ __forceinline__ Frame frame_at(char *p, int m, int n, int W, int nP)
     f.rows = reinterpret_cast<uint64_t *>(q);
     q += 256LL * W * ((n + 31) >> 5);
     f.rep = nullptr;
-    f.dup = nullptr;
+    f.pre = nullptr;
     if (kPrune) {
         f.rep = reinterpret_cast<int32_t *>(q);
         q += pad16(4LL * nP);
-        f.dup = reinterpret_cast<uint64_t *>(q);
-        q += pad16(8LL * ((nP + 63) >> 6));
+        f.pre = reinterpret_cast<int32_t *>(q);
+        q += pad16(4LL * nP);
     }
     f.R = reinterpret_cast<int32_t *>(q);
     return f;
@@ -361,6 +361,30 @@ __device__ __forceinline__ void warp_sort(Ctx &c, uint64_t *k0, int32_t *v0, uin
                                           int key_bits)
 {
     warp_sort_impl(c.lane, c.hist, k0, v0, k1, v1, n, key_bits);
+}
+
+// Pruned variant: the twin sections (rep, pre) of a new frame D whose n P
+// rows (W words, m bits) follow its off Q rows. Frames of at most 32 P rows
+// take one warp match; larger ones (or a digest collision) one sort of
+// (digest, position) keys. The sort lists are free again here (P' is in the
+// frame).
+// Out of line, as in the column kernel: it runs once per frame, and inlined
+// it crowds the node loop out of the instruction cache.
+__device__ __noinline__ void twin_sections(int lane, uint32_t *hist, const uint64_t *rows, int32_t *rep, int32_t *pre,
+                                           uint64_t *k0, int32_t *v0, uint64_t *k1, int32_t *v1, int W, int off, int n,
+                                           int m)
+{
+    if (n <= 32 && twins::twin_small(lane, rows, W, off, n, rep, pre)) return;
+    twins::twin_keys(lane, rows, W, off, n, m, k0, v0);
+    warp_sort_impl(lane, hist, k0, v0, k1, v1, n, twins::twin_key_bits(n, m));
+    twins::twin_assign(lane, rows, W, off, n, m, k0, v0, rep);
+    twins::set_pre(lane, rep, n, pre);
+}
+
+__device__ __forceinline__ void frame_twins(int lane, uint32_t *hist, const Scratch &S, const Frame &D, int W, int off,
+                                            int n, int m)
+{
+    twin_sections(lane, hist, D.rows, D.rep, D.pre, S.pkey2, S.psrc2, S.pkey, S.psrc, W, off, n, m);
 }
 
 // ---------------------------------------------------------------- row scans
@@ -576,9 +600,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
                 rejected = true;
                 break;
             }
-            // removed candidates (P positions before x with an earlier twin)
-            // are in neither P nor Q
-            const bool part = valid && cnt[u] > 0 && !(kPrune && k >= nQ && F.rep[k - nQ] < k - nQ);
+            const bool part = valid && cnt[u] > 0;
             const unsigned bal = __ballot_sync(kFull, part);
             if (part) S.qsrc[qn + __popc(bal & lanemask_lt())] = k;
             qn += __popc(bal);
@@ -588,10 +610,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         // as below, with Q = the inherited Q and the P entries popped before
         // x (the removed ones are not); the later rows are added after the
         // expansion has counted the ones still in P
-        int nrm = 0;
-        for (int w = lane; w < ((i + 63) >> 6); w += 32)
-            nrm += __popcll(F.dup[w] & ((w + 1) * 64 <= i ? ~0ULL : ((1ULL << (i & 63)) - 1)));
-        nrm = (int)__reduce_add_sync(kFull, (unsigned)nrm);
+        const int nrm = F.pre[i];
         const uint64_t nq = (uint64_t)(kx - nrm), rows = (uint64_t)W * nq, cols = (uint64_t)mp * ((nq + 63) >> 6);
         c.bytes += 8ULL * ((uint64_t)W + (rows < cols ? rows : cols));
     } else {
@@ -603,6 +622,23 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     if (rejected) {
         if (lane == 0) tadd(a, c, 1, t_scan);
         return nullptr;
+    }
+    if constexpr (kPrune) {
+        // Q' without the removed candidates (P positions before x with an
+        // earlier twin), which are in neither P nor Q: the check above kept
+        // them (a removed vertex answers as its representative does)
+        int kept = 0;
+        for (int b = 0; b < qn; b += 32) {
+            const int t = b + lane;
+            const int k = t < qn ? S.qsrc[t] : 0;
+            const bool keep = t < qn && !(k >= nQ && F.rep[k - nQ] < k - nQ);
+            const unsigned kb = __ballot_sync(kFull, keep);
+            __syncwarp();
+            if (keep) S.qsrc[kept + __popc(kb & lanemask_lt())] = k;
+            kept += __popc(kb);
+        }
+        __syncwarp();
+        qn = kept;
     }
 
     // Step 4: maximal expansion over positions (kx, n).
@@ -688,11 +724,9 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     compact_ids(c, F.Lid, Lw, W, D.Lid);
     build_child_rows(c, F.rows, W, S.qsrc, qn, S.psrc, pn, D.rows, Wd);
     if (kPrune) {
-        // twin classes of P' (the sort lists are free again: P' is in the frame)
-        twins::twin_keys(lane, D.rows, Wd, qn, pn, mp, S.pkey2, S.psrc2);
-        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, mp));
-        twins::twin_assign(lane, D.rows, Wd, qn, pn, mp, S.pkey2, S.psrc2, D.rep);
-        twins::set_dup(lane, D.rep, pn, 0, D.dup, (pn + 63) >> 6);
+        const uint64_t t_tw = tnow(a);
+        frame_twins(lane, c.hist, S, D, Wd, qn, pn, mp);
+        if (lane == 0) tadd(a, c, 22, t_tw);
     }
     if (a.emit) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
     if (lane == 0) {
@@ -1026,11 +1060,9 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     for (int k = lane; k < d; k += 32) D.Lid[k] = G.u_adj[ro + k];
     build_child_rows(c, S.urows, W, S.qsrc, qn, S.psrc, pn, D.rows, W);
     if (kPrune) {
-        // twin classes of P' (the sort lists are free again: P' is in the frame)
-        twins::twin_keys(lane, D.rows, W, qn, pn, d, S.pkey2, S.psrc2);
-        warp_sort(c, S.pkey2, S.psrc2, S.pkey, S.psrc, pn, twins::twin_key_bits(pn, d));
-        twins::twin_assign(lane, D.rows, W, qn, pn, d, S.pkey2, S.psrc2, D.rep);
-        twins::set_dup(lane, D.rep, pn, 0, D.dup, (pn + 63) >> 6);
+        const uint64_t t_tw = tnow(a);
+        frame_twins(lane, c.hist, S, D, W, qn, pn, d);
+        if (lane == 0) tadd(a, c, 22, t_tw);
     }
     if (a.emit)
         for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];

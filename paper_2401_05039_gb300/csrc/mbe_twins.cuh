@@ -16,7 +16,8 @@
 // position order, and a row's representative is the first row of its group
 // with the same words (compared word by word when the digest is a hash).
 // The kernels sort with their own warp radix sort between twin_keys and
-// twin_assign.
+// twin_assign. pre[j] counts the removed positions before j (the byte
+// count's |Q| at a pop).
 #pragma once
 #include <stdint.h>
 
@@ -109,22 +110,49 @@ __device__ void twin_assign(int lane, const uint64_t *rows, int W, int off, int 
     __syncwarp();
 }
 
-// The removal mask: bit qpos + j of dup (QW words, zeroed here) for every
-// position j < n with rep[j] < j.
-__device__ void set_dup(int lane, const int32_t *rep, int n, int qpos, uint64_t *dup, int QW)
+// Frames of at most 32 P rows (the common case): one lane per row, and
+// equal rows found by one warp match on the row itself (W = 1) or on its
+// digest, the digest match confirmed word by word. Returns false, having
+// written nothing, when a digest matched rows that differ (then the sort
+// path decides).
+__device__ bool twin_small(int lane, const uint64_t *rows, int W, int off, int n, int32_t *rep, int32_t *pre)
 {
-    for (int w = lane; w < QW; w += 32) dup[w] = 0;
+    const bool valid = lane < n;
+    uint64_t d = 0;
+    if (valid) {
+        if (W == 1) {
+            d = rows[tile_word(off + lane, 0, 1)];
+        } else {
+            d = 0x9e3779b97f4a7c15ULL;
+            for (int w = 0; w < W; ++w) d = row_digest(d, rows[tile_word(off + lane, w, W)]);
+        }
+    }
+    const unsigned vm = __ballot_sync(kFullMask, valid);
+    const unsigned grp = __match_any_sync(kFullMask, d) & vm;
+    const int leader = valid ? __ffs(grp) - 1 : lane;
+    bool ok = true;
+    if (W > 1 && valid && leader != lane)
+        for (int w = 0; w < W && ok; ++w)
+            ok = rows[tile_word(off + leader, w, W)] == rows[tile_word(off + lane, w, W)];
+    if (!__all_sync(kFullMask, ok)) return false;
+    const unsigned rm = __ballot_sync(kFullMask, valid && leader < lane);
+    if (valid) {
+        rep[lane] = leader;
+        pre[lane] = __popc(rm & ((1u << lane) - 1u));
+    }
     __syncwarp();
+    return true;
+}
+
+// pre[j] = how many positions before j are removed (rep[k] < k), j < n.
+__device__ void set_pre(int lane, const int32_t *rep, int n, int32_t *pre)
+{
+    int carry = 0;
     for (int base = 0; base < n; base += 32) {
         const int k = base + lane;
         const unsigned b = __ballot_sync(kFullMask, k < n && rep[k] < k);
-        if (lane == 0 && b) {
-            const int p = qpos + base;
-            dup[p >> 6] |= (uint64_t)b << (p & 63);
-            // the bits past the word's end, if any (their word lies inside the mask)
-            const uint64_t hi = (p & 63) > 32 ? (uint64_t)b >> (64 - (p & 63)) : 0ULL;
-            if (hi) dup[(p >> 6) + 1] |= hi;
-        }
+        if (k < n) pre[k] = carry + __popc(b & ((1u << lane) - 1u));
+        carry += __popc(b);
     }
     __syncwarp();
 }
