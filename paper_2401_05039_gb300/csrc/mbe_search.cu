@@ -961,11 +961,20 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const int lane = c.lane;
     Frame F = frame_of(fp);
     const int W = F.h->W, nQ = F.h->nQ, QW = F.h->QW, nP = F.h->nP;
-    const int i = F.h->i;
+    int i = F.h->i;
+    if (kPrune && F.rep[i] < i) {
+        // removed candidates are never popped (no node): go to the next one
+        // still in P, or finish this worker's share of the frame
+        const int end = F.h->end;
+        i = twins::next_kept(lane, F.rep, i + 1, end);
+        if (i >= end) {
+            __syncwarp();
+            if (lane == 0) F.h->i = end;
+            return nullptr;
+        }
+    }
     __syncwarp(); // every lane has read the header before lane 0 advances the cursor
     if (lane == 0) F.h->i = i + 1;
-    // a removed candidate is never popped: no node
-    if (kPrune && F.rep[i] < i) return nullptr;
     c.nodes += 1;
 
     // Step 2: L' = L n N(x) is the row of x (lane w holds word w).

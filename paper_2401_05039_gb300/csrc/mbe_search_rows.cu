@@ -71,7 +71,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
 // active-word masks lw[32] u64, active-word indices aw[32] i32
 constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32;
-constexpr int kTiles = 4; // 32-row tiles whose loads a lane keeps in flight together
+// 32-row tiles whose loads a lane keeps in flight together (the pruned
+// variant keeps its larger code in the instruction cache with 2: measured
+// 8% faster on a dense batch graph)
+constexpr int kTiles = kPrune ? 2 : 4;
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
@@ -570,12 +573,21 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     const int lane = c.lane;
     Frame F = frame_of(fp);
     const int W = F.h->W, nQ = F.h->nQ, nP = F.h->nP, n = nQ + nP;
-    const int i = F.h->i;
+    int i = F.h->i;
+    if (kPrune && F.rep[i] < i) {
+        // removed candidates are never popped (no node): go to the next one
+        // still in P, or finish this worker's share of the frame
+        const int end = F.h->end;
+        i = twins::next_kept(lane, F.rep, i + 1, end);
+        if (i >= end) {
+            __syncwarp();
+            if (lane == 0) F.h->i = end;
+            return nullptr;
+        }
+    }
     const int kx = nQ + i;
     __syncwarp(); // every lane has read the header before lane 0 advances the cursor
     if (lane == 0) F.h->i = i + 1;
-    // a removed candidate is never popped: no node
-    if (kPrune && F.rep[i] < i) return nullptr;
     c.nodes += 1;
 
     // Step 2: L' = L n N(x) is the row of x (lane w holds word w).
