@@ -102,7 +102,7 @@ int g_debug_warps = 0;
 } // namespace
 unsigned long long *debug_buffer(int n_warps)
 {
-    if (!getenv("MBE_DEBUG_TRACE")) return nullptr;
+    if (!getenv("MBE_DEBUG_TRACE") || !search_trace_compiled()) return nullptr;
     if (g_debug_warps < n_warps) {
         cudaFree(g_debug);
         g_debug = nullptr;

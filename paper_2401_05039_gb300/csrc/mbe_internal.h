@@ -146,6 +146,10 @@ cudaError_t launch_search(const SearchArgs &a, int blocks, int threads, cudaStre
 // Bytes of per-warp shared memory the search kernel uses.
 int search_smem_per_warp();
 
+// 1 when the search kernels were built with their progress records and
+// phase timers (MBE_TRACE = 1), else 0.
+int search_trace_compiled();
+
 // The column-layout kernel's variant with the sorted-list path
 // (mbe_search_lists.cu); launch_search dispatches to it when args.lists.
 cudaError_t launch_search_lists(const SearchArgs &a, int blocks, int threads, cudaStream_t stream);

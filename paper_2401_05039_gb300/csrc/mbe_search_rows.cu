@@ -242,9 +242,15 @@ __device__ __forceinline__ void trace(const SearchArgs &a, const Ctx &c, int pha
 }
 
 // debug phase timer: ns since `since` added to bucket b (lane 0 only; no-op without tracing)
+// MBE_TRACE = 1 compiles in the per-worker progress records and phase
+// timers (mbe_debug_trace); off by default: the checks and timer reads cost
+// the search 5-13% (measured on all five workloads).
+#ifndef MBE_TRACE
+#define MBE_TRACE 0
+#endif
 __device__ __forceinline__ uint64_t tnow(const SearchArgs &a)
 {
-    return a.debug ? globaltimer() : 0;
+    return (MBE_TRACE && a.debug) ? globaltimer() : 0;
 }
 __device__ __forceinline__ void tadd(const SearchArgs &a, Ctx &c, int b, uint64_t since)
 {
@@ -1318,7 +1324,7 @@ __global__ void __launch_bounds__(256, 2) MBE_ROWS_KERNEL(SearchArgs a)
     c.lw = reinterpret_cast<uint64_t *>(my + 256 + 32 + 32 * 7 * 2);
     c.aw = reinterpret_cast<int32_t *>(my + 256 + 32 + 32 * 7 * 2 + 64);
     c.na = 0;
-    c.dbg = a.debug ? a.debug + (int64_t)MBE_TRACE_WORDS * c.wid : nullptr;
+    c.dbg = (MBE_TRACE && a.debug) ? a.debug + (int64_t)MBE_TRACE_WORDS * c.wid : nullptr;
     c.arena = a.arena + (int64_t)c.wid * a.arena_bytes;
     c.mark = a.mark + (int64_t)c.wid * a.mark_stride;
     {
