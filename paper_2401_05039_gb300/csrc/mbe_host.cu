@@ -297,8 +297,9 @@ int run_search(Workspace &ws, const RunInput &in, const mbe_options &o, cudaStre
         a.max_words = o.bitset_max_words > 0 ? std::min(o.bitset_max_words, kMaxBitsetWords) : kMaxBitsetWords;
         a.min_r = std::max(1, o.min_r);
         a.min_l = std::max(1, o.min_l);
-        // the extended kernel variant: some root needs the sorted-list path, or a size filter is set
-        a.lists = (in.max_deg > 64 * a.max_words || a.min_r > 1 || a.min_l > 1) ? 1 : 0;
+        // the extended kernel variant: some root needs the sorted-list path, a size filter is set, or the
+        // bicliques are written
+        a.lists = (in.max_deg > 64 * a.max_words || a.min_r > 1 || a.min_l > 1 || (o.emit && bic)) ? 1 : 0;
         // the pruned variant carries the size filter too (and no list path)
         a.prune = in.prune;
         a.trep = in.trep;

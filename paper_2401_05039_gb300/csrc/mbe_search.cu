@@ -73,6 +73,10 @@ constexpr bool kExt = MBE_LIST_PATH != 0 || MBE_PRUNE != 0;
 // The pruned variant: every frame carries, per P entry, the first position
 // of its twin class (rep, see twin_reps) and a removal mask over X.
 constexpr bool kPrune = MBE_PRUNE != 0;
+// Biclique output runs in the extended variants only (the host launches
+// one of them when the bicliques are asked for): the plain kernels carry no
+// output code in their node loop.
+__device__ __forceinline__ bool emitting(const SearchArgs &a) { return kExt && a.emit; }
 
 constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
@@ -1039,9 +1043,9 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
             const bool part = valid && cnt[u] > 0 && cnt[u] < mp && (!kExt || cnt[u] >= a.min_l);
             const int g = (full || part) ? F.gid[k] : 0;
             if (full) rsum += key_u(g);
-            if (a.emit || (kExt && a.min_r > 1)) {
+            if (emitting(a) || (kExt && a.min_r > 1)) {
                 const unsigned fb = __ballot_sync(kFull, full);
-                if (a.emit && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = g;
+                if (emitting(a) && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = g;
                 nfull += __popc(fb);
             }
             const unsigned bal = __ballot_sync(kFull, part);
@@ -1068,7 +1072,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     }
 
     uint64_t t_build = tnow(a);
-    if (a.emit) {
+    if (emitting(a)) {
         // B = {x} and the candidates that joined R', ascending
         if (lane == 0) S.rtmp[nfull] = xg;
         __syncwarp();
@@ -1089,7 +1093,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     // that shrinks the columns to at most kCompressNum/kCompressDen of the
     // prefix, else the prefix is copied with its holes.
     const int Wd = (mp + 63) >> 6;
-    const int nRd = a.emit ? F.h->nR + 1 + nfull : 0;
+    const int nRd = emitting(a) ? F.h->nR + 1 + nfull : 0;
     char *cp = fp + F.h->bytes;
     if ((uintptr_t)cp & 15) {
         if (lane == 0) set_error(a, kErrInternal);
@@ -1165,7 +1169,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         c.dbg[26] += now - t_tr;
         c.dbg[27] += compress ? 0 : 1;
     }
-    if (a.emit) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
+    if (emitting(a)) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
     if (lane == 0) {
         FrameHdr h;
         h.m = mp;
@@ -1208,7 +1212,7 @@ __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv
     const int W = (mp + 63) >> 6, n = nQd + pn;
     const int64_t tiles = (n + 31) >> 5;
     const int QW = (n + 63) >> 6;
-    const int nRd = a.emit ? na + nb : 0;
+    const int nRd = emitting(a) ? na + nb : 0;
     const int64_t sz = frame_bytes(mp, QW, pn, W, nRd);
     if (n > e.ncap || tiles * W * 32 > e.urow_words || ((uintptr_t)cp & 15) || cp + sz > e.limit) {
         if (lane == 0) set_error(a, kErrArena);
@@ -1238,7 +1242,7 @@ __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv
     __syncwarp();
     if (nQd > 0) rows_to_columns(lane, urows, W, nullptr, nQd, mp, D.Q, QW, 0);
     rows_to_columns(lane, D.rows, W, nullptr, pn, mp, D.Q, QW, nQd);
-    if (a.emit) emit::merge_into(lane, Ra, na, Rb, nb, D.R);
+    if (emitting(a)) emit::merge_into(lane, Ra, na, Rb, nb, D.R);
     if (lane == 0) {
         FrameHdr h;
         h.m = mp;
@@ -1343,7 +1347,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     // (Not when the bicliques are written: they list L in id order, which the
     // level sets then keep.)
     const int32_t *Ln = G.u_adj + ro;
-    if (!a.emit && d > 1 && d <= S.ncap) {
+    if (!emitting(a) && d > 1 && d <= S.ncap) {
         int64_t sdeg = 0;
         for (int j = lane; j < d; j += 32) {
             const int w = G.u_adj[ro + j];
@@ -1470,9 +1474,9 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         bool qpart = ql;
         bool ppart = valid && !removed && !earlier && cnt < d && (!kExt || cnt >= a.min_l);
         if (full) rsum += key_u(u);
-        if (a.emit || (kExt && a.min_r > 1)) {
+        if (emitting(a) || (kExt && a.min_r > 1)) {
             unsigned fb = __ballot_sync(kFull, full);
-            if (a.emit && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
+            if (emitting(a) && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
             nfull += __popc(fb);
         }
         unsigned qb = __ballot_sync(kFull, qpart);
@@ -1498,7 +1502,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     }
 
     prepare_masks(c, Lw, W);
-    if (a.emit) {
+    if (emitting(a)) {
         // R' = {r} and the candidates that joined it, ascending; L' = N(r)
         if (lane == 0) S.rtmp[nfull] = r;
         __syncwarp();
@@ -1526,7 +1530,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     }
 
     const int QW = (qn + pn + 63) >> 6;
-    const int nRd = a.emit ? 1 + nfull : 0;
+    const int nRd = emitting(a) ? 1 + nfull : 0;
     const int64_t sz = frame_bytes(d, QW, pn, W, nRd);
     char *cp = c.arena;
     if (cp + sz > c.limit) {
@@ -1551,7 +1555,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         if (lane == 0) tadd(a, c, 22, t_tw);
     }
     rows_to_columns(lane, D.rows, W, nullptr, pn, d, D.Q, QW, qn, D.rep);
-    if (a.emit)
+    if (emitting(a))
         for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {
         FrameHdr h;

@@ -66,6 +66,10 @@ constexpr bool kExt = MBE_LIST_PATH != 0 || MBE_PRUNE != 0;
 // The pruned variant: every frame carries, per P entry, the first position
 // of its twin class (twins::twin_reps) and a removal mask over P.
 constexpr bool kPrune = MBE_PRUNE != 0;
+// Biclique output runs in the extended variants only (the host launches
+// one of them when the bicliques are asked for): the plain kernels carry no
+// output code in their node loop.
+__device__ __forceinline__ bool emitting(const SearchArgs &a) { return kExt && a.emit; }
 
 constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
@@ -678,9 +682,9 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
             const bool part = valid && cnt[u] > 0 && cnt[u] < mp && (!kExt || cnt[u] >= a.min_l);
             const int g = (full || part) ? F.gid[k] : 0;
             if (full) rsum += key_u(g);
-            if (a.emit || (kExt && a.min_r > 1)) {
+            if (emitting(a) || (kExt && a.min_r > 1)) {
                 const unsigned fb = __ballot_sync(kFull, full);
-                if (a.emit && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = g;
+                if (emitting(a) && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = g;
                 nfull += __popc(fb);
             }
             const unsigned bal = __ballot_sync(kFull, part);
@@ -709,8 +713,8 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     if (kExt && pn > 0 && (mp - 1 < a.min_l || rn + pn < a.min_r)) pn = 0;
 
     uint64_t t_build = tnow(a);
-    if (a.emit || pn > 0) prepare_masks(c, Lw, W);
-    if (a.emit) {
+    if (emitting(a) || pn > 0) prepare_masks(c, Lw, W);
+    if (emitting(a)) {
         // B = {x} and the candidates that joined R', ascending
         if (lane == 0) S.rtmp[nfull] = xg;
         __syncwarp();
@@ -725,7 +729,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
     // Child frame: [Q' | P' sorted by (count, id)], rows packed to L'.
     const int Wd = (mp + 63) >> 6;
     const int nd = qn + pn;
-    const int nRd = a.emit ? F.h->nR + 1 + nfull : 0;
+    const int nRd = emitting(a) ? F.h->nR + 1 + nfull : 0;
     const int64_t sz = frame_bytes(mp, nd, Wd, nRd, pn);
     char *cp = fp + F.h->bytes;
     if (cp + sz > c.limit) {
@@ -746,7 +750,7 @@ __device__ char *process_node(const SearchArgs &a, Ctx &c, char *fp)
         frame_twins(lane, c.hist, S, D, Wd, qn, pn, mp);
         if (lane == 0) tadd(a, c, 22, t_tw);
     }
-    if (a.emit) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
+    if (emitting(a)) emit::merge_into(lane, F.R, F.h->nR, S.rtmp, nfull + 1, D.R);
     if (lane == 0) {
         FrameHdr h;
         h.m = mp;
@@ -783,7 +787,7 @@ __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv
     const int lane = e.lane;
     const int W = (mp + 63) >> 6, n = nQd + pn;
     const int64_t tiles = (n + 31) >> 5;
-    const int nRd = a.emit ? na + nb : 0;
+    const int nRd = emitting(a) ? na + nb : 0;
     const int64_t sz = frame_bytes(mp, n, W, nRd, pn);
     if (n > e.ncap || ((uintptr_t)cp & 15) || cp + sz > e.limit) {
         if (lane == 0) set_error(a, kErrArena);
@@ -804,7 +808,7 @@ __device__ __noinline__ char *bits_from_lists(const SearchArgs &a, const ListEnv
         atomicOr(reinterpret_cast<unsigned long long *>(&rows[row_word(k, j >> 6, W)]), 1ULL << (j & 63));
     });
     for (int k = lane; k < n; k += 32) e.mark[D.gid[k]] = -1;
-    if (a.emit) emit::merge_into(lane, Ra, na, Rb, nb, D.R);
+    if (emitting(a)) emit::merge_into(lane, Ra, na, Rb, nb, D.R);
     __syncwarp();
     if (lane == 0) {
         FrameHdr h;
@@ -1005,9 +1009,9 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         bool qpart = ql;
         bool ppart = valid && !removed && !earlier && cnt < d && (!kExt || cnt >= a.min_l);
         if (full) rsum += key_u(u);
-        if (a.emit || (kExt && a.min_r > 1)) {
+        if (emitting(a) || (kExt && a.min_r > 1)) {
             unsigned fb = __ballot_sync(kFull, full);
-            if (a.emit && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
+            if (emitting(a) && full) S.rtmp[nfull + __popc(fb & lanemask_lt())] = u;
             nfull += __popc(fb);
         }
         unsigned qb = __ballot_sync(kFull, qpart);
@@ -1033,7 +1037,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     }
 
     prepare_masks(c, Lw, W);
-    if (a.emit) {
+    if (emitting(a)) {
         // R' = {r} and the candidates that joined it, ascending; L' = N(r)
         if (lane == 0) S.rtmp[nfull] = r;
         __syncwarp();
@@ -1061,7 +1065,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
     }
 
     const int nd = qn + pn;
-    const int nRd = a.emit ? 1 + nfull : 0;
+    const int nRd = emitting(a) ? 1 + nfull : 0;
     const int64_t sz = frame_bytes(d, nd, W, nRd, pn);
     char *cp = c.arena;
     if (cp + sz > c.limit) {
@@ -1082,7 +1086,7 @@ __device__ bool process_root(const SearchArgs &a, Ctx &c, const GView &G, int r,
         frame_twins(lane, c.hist, S, D, W, qn, pn, d);
         if (lane == 0) tadd(a, c, 22, t_tw);
     }
-    if (a.emit)
+    if (emitting(a))
         for (int k = lane; k <= nfull; k += 32) D.R[k] = S.rtmp[k];
     if (lane == 0) {
         FrameHdr h;
