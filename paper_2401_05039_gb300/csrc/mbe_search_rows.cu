@@ -75,10 +75,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // per-warp shared memory (u32 units): hist[256] u32, off[32] i32, masks [32][7] u64,
 // active-word masks lw[32] u64, active-word indices aw[32] i32
 constexpr int kSmemWords = 256 + 32 + 32 * 7 * 2 + 32 * 2 + 32;
-// 32-row tiles whose loads a lane keeps in flight together (the pruned
-// variant keeps its larger code in the instruction cache with 2: measured
-// 8% faster on a dense batch graph)
-constexpr int kTiles = kPrune ? 2 : 4;
+// 32-row tiles whose loads a lane keeps in flight together: 2 keeps the
+// node loop in the instruction cache (measured against 4 and 8: the dense
+// batch graph 2867 in 241 / 277 / 413 ms, planted 5k in 25.9 / 26.1 / 35.1)
+constexpr int kTiles = 2;
 
 __device__ __forceinline__ unsigned lanemask_lt()
 {
