@@ -1617,11 +1617,55 @@ __device__ bool warp_copy(char *dst, const char *src, int64_t bytes, int lane, b
     return true;
 }
 
+// The frame walk and copy of a donation: 1 when a frame was published, -1
+// when the copy failed (the run aborts), 0 when no frame qualified. Out of
+// line: it runs rarely, and the node loop keeps its instruction-cache room
+// (measured: planted 5k 37.9 -> 35.3 ms, Chung-Lu 200k 477 -> 452 ms).
+__device__ __noinline__ int donate_frame(const SearchArgs &a, int lane, int wid, char *arena, char *top)
+{
+    // walk frames from the bottom of the stack
+    char *fp = arena;
+    while (true) {
+        FrameHdr *h = reinterpret_cast<FrameHdr *>(fp);
+        int left = h->end - h->i;
+        if (left >= 2 && h->bytes <= a.slot_bytes && h->bytes <= a.stack_bytes) {
+            int mid = h->i + (left + 1) / 2;
+            char *slot = a.slots + (int64_t)wid * a.slot_bytes;
+            if (lane == 0) {
+                a.slot_state[wid] = kSlotWriting;
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), 1ULL);
+            }
+            __syncwarp();
+            if (!warp_copy(slot, fp, h->bytes, lane, false)) {
+                if (lane == 0) {
+                    set_error(a, kErrInternal);
+                    atomicExch(a.slot_state + wid, kSlotEmpty);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), ~0ULL);
+                }
+                return -1;
+            }
+            if (lane == 0) {
+                FrameHdr *sh = reinterpret_cast<FrameHdr *>(slot);
+                sh->i = mid;
+                sh->parent = -1;
+                h->end = mid;
+                __threadfence();
+                atomicExch(a.slot_state + wid, kSlotFull);
+                atomicAdd(a.n_published, 1);
+            }
+            __syncwarp();
+            return 1;
+        }
+        if (fp == top) return 0;
+        fp += h->bytes;
+    }
+}
+
 // If some worker is idle and this worker's slot is free, give away the upper
 // half of the remaining candidates of its shallowest frame that has at least
 // two left: the copy keeps every candidate (earlier positions stay Q-like
 // for the thief), with i = mid; this worker keeps [i, mid).
-__device__ void maybe_donate(const SearchArgs &a, Ctx &c, char *top)
+__device__ __forceinline__ void maybe_donate(const SearchArgs &a, Ctx &c, char *top)
 {
     const int lane = c.lane;
     int idle = 0, state = 0;
@@ -1633,45 +1677,12 @@ __device__ void maybe_donate(const SearchArgs &a, Ctx &c, char *top)
     idle = __shfl_sync(kFull, idle, 0);
     state = __shfl_sync(kFull, state, 0);
     if (idle <= 0 || state != kSlotEmpty) return;
-    // walk frames from the bottom of the stack
-    char *fp = c.arena;
-    while (true) {
-        FrameHdr *h = reinterpret_cast<FrameHdr *>(fp);
-        int left = h->end - h->i;
-        if (left >= 2 && h->bytes <= a.slot_bytes && h->bytes <= a.stack_bytes) {
-            int mid = h->i + (left + 1) / 2;
-            char *slot = a.slots + (int64_t)c.wid * a.slot_bytes;
-            if (lane == 0) {
-                a.slot_state[c.wid] = kSlotWriting;
-                atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), 1ULL);
-            }
-            __syncwarp();
-            uint64_t t_cp = tnow(a);
-            if (!warp_copy(slot, fp, h->bytes, lane, false)) {
-                if (lane == 0) {
-                    set_error(a, kErrInternal);
-                    atomicExch(a.slot_state + c.wid, kSlotEmpty);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.outstanding), ~0ULL);
-                }
-                c.abort = true;
-                return;
-            }
-            if (lane == 0) tadd(a, c, 3, t_cp);
-            if (lane == 0) {
-                FrameHdr *sh = reinterpret_cast<FrameHdr *>(slot);
-                sh->i = mid;
-                sh->parent = -1;
-                h->end = mid;
-                __threadfence();
-                atomicExch(a.slot_state + c.wid, kSlotFull);
-                atomicAdd(a.n_published, 1);
-            }
-            __syncwarp();
-            c.t_don += 1;
-            return;
-        }
-        if (fp == top) return;
-        fp += h->bytes;
+    const uint64_t t_cp = tnow(a);
+    const int r = donate_frame(a, lane, c.wid, c.arena, top);
+    if (r < 0) c.abort = true;
+    if (r > 0) {
+        c.t_don += 1;
+        if (lane == 0) tadd(a, c, 3, t_cp);
     }
 }
 
