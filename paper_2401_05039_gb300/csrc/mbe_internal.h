@@ -112,9 +112,8 @@ constexpr int kMaxBitsetWords = 32;
 // candidates. A bitset frame (level set of w <= 64 * kMaxBitsetWords
 // vertices): header, L ids, X columns (w x ceil(nc/64) words), P ids, P
 // rows (32-row tiles of ceil(w/64) words), the pruned variant's twin
-// positions (one int32 per P entry) and removal mask (one bit per X
-// position), R ids. A list frame (a wider level set): header, L ids, Q ids,
-// P ids, R ids.
+// sections (two int32 per P entry), R ids. A list frame (a wider level
+// set): header, L ids, Q ids, P ids, R ids.
 #if defined(__CUDACC__)
 __host__ __device__
 #endif
@@ -124,7 +123,7 @@ inline int64_t level1_frame_bound(int64_t d, int64_t nc)
     const int64_t w = d < 64 * kMaxBitsetWords ? d : 64 * kMaxBitsetWords;
     const int64_t W = (w + 63) / 64;
     const int64_t bits = kFrameHdrBytes + p16(4 * w) + p16(8 * w * ((nc + 63) / 64)) + p16(4 * nc) +
-                         256 * W * ((nc + 31) / 32) + p16(4 * nc) + p16(8 * ((nc + 63) / 64)) + p16(4 * (nc + 1));
+                         256 * W * ((nc + 31) / 32) + 2 * p16(4 * nc) + p16(4 * (nc + 1));
     const int64_t list = kFrameHdrBytes + p16(4 * d) + 2 * p16(4 * nc) + p16(4 * (nc + 1));
     return d > w && list > bits ? list : bits;
 }

@@ -64,7 +64,8 @@ namespace {
 // The extended variants (list path, pruning) also carry the size filter.
 constexpr bool kExt = MBE_LIST_PATH != 0 || MBE_PRUNE != 0;
 // The pruned variant: every frame carries, per P entry, the first position
-// of its twin class (twins::twin_reps) and a removal mask over P.
+// of its twin class and the number of removed entries before it
+// (mbe_twins.cuh).
 constexpr bool kPrune = MBE_PRUNE != 0;
 // Biclique output runs in the extended variants only (the host launches
 // one of them when the bicliques are asked for): the plain kernels carry no
