@@ -174,6 +174,25 @@ def test_planted5k_whole_graph(mbe, golden_dir, layout):
     G.close()
 
 
+def test_chunglu200k_whole_graph(mbe, golden_dir):
+    # the pruned whole-graph oracle total of the 200k x 1M Chung-Lu workload,
+    # and its stored per-root rows (the column layout, as chosen automatically)
+    import torch
+    gold = _golden(golden_dir, "chunglu200k_prune")
+    g = synth.workload("chunglu200k")
+    assert g.digest() == gold["graph"]["digest"]
+    G = mbe.Graph.from_synth(g)
+    out = torch.zeros((g.nU, 4), dtype=torch.int64, device="cuda")
+    r = G.enumerate(per_root=out, prune=1)
+    got = out.cpu().numpy().view(np.uint64)
+    t = gold["total"]
+    assert gpu_tuple(r) == (t["count"], int(t["hash"], 16), t["nodes"], t["bytes"])
+    for root, row in gold["per_root"].items():
+        assert tuple(int(x) for x in got[int(root)]) == (row["count"], int(row["hash"], 16), row["nodes"],
+                                                         row["bytes"]), root
+    G.close()
+
+
 def test_sampled_roots_of_the_large_workloads(mbe):
     # per-root rows of seeded random roots, oracle run live
     import torch
