@@ -218,9 +218,16 @@ def prefix_sample(name, g, threads, seed=20240110, batch=256, keep_rows=300, pro
             rows = d["rows"]
             model = int(d["bytes_model"]) if "bytes_model" in d else 1
     t0 = time.time()
+    # heaviest roots of a batch first (two-hop volume), so that no thread is
+    # left alone with a late heavy root; the rows keep the permutation order
+    deg_v = np.diff(g.v_off)
+    volume = np.array([int(deg_v[g.u_adj[g.u_off[r]:g.u_off[r + 1]]].sum()) for r in range(g.nU)], dtype=np.int64)
     while rows.shape[0] < perm.size and (time_budget is None or time.time() - t0 < time_budget):
         k = rows.shape[0]
-        part = oracle.per_root(g, roots=perm[k:k + batch], nthreads=threads, bytes_b=True)
+        roots = perm[k:k + batch]
+        heavy = np.argsort(-volume[roots], kind="stable")
+        part = np.empty((roots.size, 5), dtype=np.uint64)
+        part[heavy] = oracle.per_root(g, roots=roots[heavy], nthreads=threads, bytes_b=True)
         rows = np.concatenate([rows, part])
         if progress:
             np.savez(progress + ".tmp.npz", rows=rows, seed=seed, digest=np.array(g.digest()),
@@ -253,6 +260,7 @@ def main():
     ap.add_argument("--prefix", action="store_true", help="resumable seeded-order per-root run (large graphs)")
     ap.add_argument("--progress", default=None, help="progress file for --prefix")
     ap.add_argument("--budget", type=float, default=None, help="seconds to spend in this --prefix invocation")
+    ap.add_argument("--batch", type=int, default=256, help="roots per oracle call in --prefix mode")
     ap.add_argument("--prune", action="store_true", help="the pruned mode: writes <name>_prune.json")
     ap.add_argument("--batch-rest", action="store_true",
                     help="add per-root rows of the batch graphs without whole-graph rows to batch4096.json")
@@ -269,7 +277,7 @@ def main():
             out = whole_graph_pruned(name, synth.workload(name), args.threads)
             suffix = "_prune"
         elif args.prefix:
-            out = prefix_sample(name, synth.workload(name), args.threads, progress=args.progress,
+            out = prefix_sample(name, synth.workload(name), args.threads, batch=args.batch, progress=args.progress,
                                 time_budget=args.budget)
         elif name == "er200x300":
             out = whole_graph(name, synth.workload(name), args.threads, n_heavy=8, n_random=24, records=True)
